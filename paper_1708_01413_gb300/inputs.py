@@ -1,0 +1,108 @@
+"""Seeded synthetic inputs for the APC solver (test and benchmark workloads).
+
+This module only draws random numbers and lays them out; it holds none of the
+method's arithmetic.  Both the CPU oracle's tests and the GPU path consume the
+arrays it returns.
+
+Workload recipes (shapes and distributions of the paper's experiments, Sec. 5,
+"Standard Gaussian" rows of Table 2, and the scaled / batched / differentiated
+variants exercised by the solver):
+
+* ``gaussian_system``  A n x n with i.i.d. N(0,1) entries, x_true ~ N(0,1),
+  b = A x_true.
+* ``scaled_system``    A = D_r G D_c, G i.i.d. N(0,1), D_r and D_c diagonal with
+  entries log-uniform in [10^-lo, 10^hi].
+* ``batch_systems``    independent systems with n ~ U{n_lo..n_hi},
+  A = G + 0.5 sqrt(n) I, uneven row blocks p_i ~ U{p_lo..p_hi} (the last block
+  truncated), k right-hand sides b ~ N(0,1).
+* ``even_offsets``     m contiguous row blocks of N/m rows.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["gaussian_system", "scaled_system", "batch_systems", "even_offsets",
+           "uneven_offsets", "target_vector", "gaussian_system_torch", "scaled_system_torch"]
+
+
+def even_offsets(N: int, m: int) -> np.ndarray:
+    """Row offsets of m contiguous blocks; the first N % m blocks get one extra row."""
+    base, extra = divmod(N, m)
+    sizes = [base + (1 if i < extra else 0) for i in range(m)]
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+
+def uneven_offsets(N: int, p_lo: int, p_hi: int, rng: np.random.Generator) -> np.ndarray:
+    """Row offsets with block sizes drawn uniformly from {p_lo..p_hi}; the
+    last block is truncated at N."""
+    offs = [0]
+    while offs[-1] < N:
+        offs.append(min(N, offs[-1] + int(rng.integers(p_lo, p_hi + 1))))
+    return np.asarray(offs, dtype=np.int64)
+
+
+def gaussian_system(n: int, seed: int, N: int | None = None, k: int = 1):
+    """(A, x_true, b): A N x n i.i.d. N(0,1), x_true n (x k) ~ N(0,1), b = A x_true."""
+    rng = np.random.default_rng(seed)
+    N = n if N is None else N
+    A = rng.standard_normal((N, n))
+    x_true = rng.standard_normal((n,) if k == 1 else (n, k))
+    return A, x_true, A @ x_true
+
+
+def scaled_system(n: int, seed: int, lo: float = 2.0, hi: float = 2.0):
+    """(A, x_true, b) with A = D_r G D_c, D entries log-uniform in [10^-lo, 10^hi]."""
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((n, n))
+    d_r = 10.0 ** rng.uniform(-lo, hi, size=n)
+    d_c = 10.0 ** rng.uniform(-lo, hi, size=n)
+    A = (d_r[:, None] * G) * d_c[None, :]
+    x_true = rng.standard_normal(n)
+    return A, x_true, A @ x_true
+
+
+def batch_systems(nsys: int, seed: int, n_lo: int = 256, n_hi: int = 4096,
+                  p_lo: int = 16, p_hi: int = 128, k: int = 32):
+    """List of (A, B, row_offsets) for ``nsys`` independent systems."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nsys):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        A = rng.standard_normal((n, n)) + 0.5 * np.sqrt(n) * np.eye(n)
+        offs = uneven_offsets(n, p_lo, p_hi, rng)
+        B = rng.standard_normal((n, k))
+        out.append((A, B, offs))
+    return out
+
+
+def target_vector(n: int, seed: int, k: int = 1) -> np.ndarray:
+    """x_target ~ N(0,1) for the differentiated loss 0.5 ||xbar_T - x_target||^2."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.standard_normal((n,) if k == 1 else (n, k))
+
+
+# Device-side generators for the full-size workloads (a host draw of 10^9
+# normals takes tens of seconds).  These use torch's own seeded generator on
+# the given device; results differ from the NumPy streams above, so a test
+# that compares against the oracle copies the device arrays back to the host.
+
+def gaussian_system_torch(n: int, seed: int, device, dtype=None):
+    import torch
+    dtype = torch.float64 if dtype is None else dtype
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = torch.randn((n, n), generator=g, device=device, dtype=dtype)
+    x_true = torch.randn((n,), generator=g, device=device, dtype=dtype)
+    return A, x_true, A @ x_true
+
+
+def scaled_system_torch(n: int, seed: int, device, lo: float = 2.0, hi: float = 2.0):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    A = torch.randn((n, n), generator=g, device=device, dtype=torch.float64)
+    d_r = 10.0 ** (torch.rand((n,), generator=g, device=device, dtype=torch.float64) * (lo + hi) - lo)
+    d_c = 10.0 ** (torch.rand((n,), generator=g, device=device, dtype=torch.float64) * (lo + hi) - lo)
+    A.mul_(d_r[:, None]).mul_(d_c[None, :])
+    x_true = torch.randn((n,), generator=g, device=device, dtype=torch.float64)
+    return A, x_true, A @ x_true
