@@ -1,0 +1,149 @@
+/*
+ * apc.h -- C ABI of the GB300 (sm_103a) Accelerated Projection-based
+ * Consensus (APC) solver for A x = b.
+ *
+ * Method (Azizan-Ruhi, Lahouti, Avestimehr, Hassibi, 2017): the N equations
+ * are split into m contiguous row blocks [A_i, b_i] (Sec. 2).  Each block
+ * keeps an iterate x_i; the master keeps xbar.  One iteration is Eq. (cons):
+ *     x_i(t+1)  = x_i(t) + gamma * P_i (xbar(t) - x_i(t))            (cons1)
+ *     xbar(t+1) = (eta/m) sum_i x_i(t+1) + (1 - eta) xbar(t)         (cons2)
+ * with P_i = I - A_i^T (A_i A_i^T)^{-1} A_i the projector onto the nullspace
+ * of A_i (Sec. 3.1), applied through an orthonormal basis Q_i of the row
+ * space of A_i (Sec. 3.3, "e.g. using QR factorization").
+ *
+ * Conventions for every entry point:
+ *   - Return value: APC_OK (0) or a negative APC_ERR_* code; the text of the
+ *     last error of a context is available from apc_last_error().
+ *   - Pointers named *_dev are CUDA device pointers; *_host are host pointers.
+ *     The caller owns every buffer it passes; nothing is retained after a call
+ *     returns except what apc_setup() copies into the context.
+ *   - Matrices are row-major with an explicit leading dimension (in elements).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it; entry points that return host values
+ *     synchronise that stream before returning.
+ *   - One context belongs to one device (the device current at apc_setup).
+ *     Calls on one context must not overlap.
+ */
+#ifndef APC_H
+#define APC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define APC_OK                  0
+#define APC_ERR_INVALID_ARG    -1  /* bad size, pointer, offsets or option     */
+#define APC_ERR_SINGULAR_BLOCK -2  /* A_i A_i^T not positive definite (Sec.3.1)*/
+#define APC_ERR_NONFINITE      -3  /* NaN/Inf in an input or an iterate        */
+#define APC_ERR_PARAMS         -4  /* (gamma, eta) outside the set S (Thm. 1)  */
+#define APC_ERR_NOT_CONVERGED  -5  /* max_iters reached before the tolerance   */
+#define APC_ERR_DIVERGED       -6  /* residual grew by > 1e8 over its start    */
+#define APC_ERR_LAUNCH         -7  /* persistent grid cannot be co-resident    */
+#define APC_ERR_TIMEOUT        -8  /* a device-side wait ran out of time       */
+#define APC_ERR_CUDA           -9  /* a CUDA runtime call failed               */
+#define APC_ERR_UNSUPPORTED   -10  /* a size outside what the kernels handle   */
+#define APC_ERR_NOMEM         -11  /* device allocation failed                 */
+
+/* Arithmetic of the iteration.  The setup (QR of the blocks) and the
+ * refinement residual are FP64 in every mode. */
+#define APC_F64  0   /* Q_i FP64, iterates FP64                            */
+#define APC_F32  1   /* Q_i FP32, iterates FP32                            */
+#define APC_BF16 2   /* Q_i BF16, iterates and accumulation FP32           */
+
+typedef struct apc_ctx apc_ctx;
+
+typedef struct apc_options {
+    int32_t precision;      /* APC_F64 / APC_F32 / APC_BF16                   */
+    int32_t cluster_size;   /* CTAs sharing one row range; 0 = automatic      */
+    double  timeout_s;      /* limit of every device-side wait; 0 = 2 s       */
+} apc_options;
+
+typedef struct apc_stats {
+    int64_t iterations;     /* APC iterations run (all sweeps)                */
+    int32_t sweeps;         /* refinement sweeps (1 without refinement)       */
+    double  rel_residual;   /* final ||b - A x||_2 / ||b||_2, FP64            */
+    double  seconds;        /* wall time of the solve on the host clock       */
+} apc_stats;
+
+/* apc_setup -- partition [A, b] into m row blocks and factor each block.
+ * Sec. 2 (partition) and Sec. 3.3 (QR).  For block i (rows
+ * row_offsets_host[i] .. row_offsets_host[i+1]-1) the rows are scaled to unit
+ * length (this leaves P_i unchanged) and A_i^T = Q_i R_i is computed by
+ * two passes of Cholesky QR in FP64.  Q_i is then stored in the precision of
+ * opt->precision.  A copy of A and b (FP64) is kept for FP64 residuals.
+ *   A_dev  : N x n, row-major, leading dimension lda >= n, FP64, device.
+ *   b_dev  : N, FP64, device.
+ *   N >= n >= 1; row_offsets_host: m+1 strictly increasing int64 with
+ *   offsets[0] = 0 and offsets[m] = N; every block has 1..256 rows and
+ *   fewer rows than n.  m <= 256.
+ * Errors: INVALID_ARG, SINGULAR_BLOCK (block index in apc_last_error),
+ * NONFINITE, NOMEM, CUDA, UNSUPPORTED.  On error *out is NULL. */
+int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t lda,
+              const double *b_dev, const int64_t *row_offsets_host, int32_t m,
+              const apc_options *opt, void *stream);
+
+/* apc_optimal_params -- Theorem 1: from mu_min, mu_max of
+ * X = (1/m) sum_i A_i^T (A_i A_i^T)^{-1} A_i return the optimal rate
+ * rho = (sqrt(kappa)-1)/(sqrt(kappa)+1) and (gamma*, eta*), the roots of
+ * z^2 - (s + 1 - rho^2) z + s with s = 4/(sqrt(mu_max)+sqrt(mu_min))^2,
+ * gamma the smaller one (S requires gamma in [0, 2]).  Pure host arithmetic.
+ * Errors: INVALID_ARG unless 0 < mu_min <= mu_max <= 1. */
+int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho);
+
+/* apc_reset -- Algorithm 1 initialisation for right-hand side rhs_dev
+ * (FP64, N, device; NULL = the b given to apc_setup): x_i(0) is the
+ * least-norm solution A_i^T (A_i A_i^T)^{-1} b_i of block i and
+ * xbar(0) = (1/m) sum_i x_i(0).  Resets the iteration counter. */
+int apc_reset(apc_ctx *ctx, const double *rhs_dev, void *stream);
+
+/* apc_iterate -- run `iters` iterations of Eq. (cons) from the current state
+ * in one persistent launch (one grid-wide barrier per iteration).  Requires
+ * 0 < gamma < 2 (Theorem 1's S; the (m-1)n eigenvalues 1 - gamma of App. A)
+ * else APC_ERR_PARAMS.  Errors: TIMEOUT, LAUNCH, CUDA. */
+int apc_iterate(apc_ctx *ctx, double gamma, double eta, int64_t iters, void *stream);
+
+/* apc_get_xbar -- copy xbar (n values) to x_dev as FP64 (device). */
+int apc_get_xbar(apc_ctx *ctx, double *x_dev, void *stream);
+
+/* apc_get_x -- copy the machines' iterates x_i (m x n, row i = x_i, FP64,
+ * device, leading dimension ldx >= n) to x_dev.  For tests and checkpoints. */
+int apc_get_x(apc_ctx *ctx, double *x_dev, int64_t ldx, void *stream);
+
+/* apc_residual -- FP64 relative residual ||r - A x||_2 / ||r||_2 of x_dev
+ * (FP64, n, device) against rhs_dev (NULL = the stored b).  If resid_dev is
+ * not NULL the residual vector r - A x (N, FP64) is written there. */
+int apc_residual(apc_ctx *ctx, const double *x_dev, const double *rhs_dev,
+                 double *resid_dev, double *rel_residual_host, void *stream);
+
+/* apc_solve -- run Algorithm 1 from the least-norm initialisation until the
+ * FP64 relative residual ||b - A xbar|| / ||b|| <= tol, checking every
+ * `check_every` iterations, or max_iters iterations.  With refine != 0 the
+ * iteration runs as the inner solver of FP64 iterative refinement:
+ * x <- x + delta, where delta is the APC solution of A delta = b - A x,
+ * stopped when its residual stagnates.  The solution (FP64, n) goes to
+ * x_dev.  Errors: NOT_CONVERGED (x_dev still holds the last iterate),
+ * DIVERGED, PARAMS, TIMEOUT, CUDA. */
+int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_iters,
+              int64_t check_every, int32_t refine, double *x_dev, apc_stats *stats,
+              void *stream);
+
+/* apc_context_info -- sizes chosen at setup: padded block width, cluster
+ * size, number of clusters and bytes of Q.  Any pointer may be NULL. */
+int apc_context_info(const apc_ctx *ctx, int64_t *n, int64_t *N, int32_t *m, int32_t *width,
+                     int32_t *cluster_size, int32_t *clusters, int64_t *q_bytes);
+
+/* apc_last_error -- text of the last error on ctx (or of the last failed
+ * apc_setup when ctx is NULL).  Valid until the next call on ctx. */
+const char *apc_last_error(const apc_ctx *ctx);
+
+/* apc_destroy -- free the context and its device buffers.  NULL is a no-op. */
+void apc_destroy(apc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APC_H */

@@ -1,0 +1,190 @@
+"""Thin ctypes binding of the C ABI in ``include/apc.h``.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libapc.so``.  PyTorch supplies device memory (tensors are passed by
+``data_ptr()``) and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libapc.so")
+
+APC_F64, APC_F32, APC_BF16 = 0, 1, 2
+PRECISIONS = {"f64": APC_F64, "f32": APC_F32, "bf16": APC_BF16}
+
+ERRORS = {
+    0: "OK", -1: "INVALID_ARG", -2: "SINGULAR_BLOCK", -3: "NONFINITE", -4: "PARAMS",
+    -5: "NOT_CONVERGED", -6: "DIVERGED", -7: "LAUNCH", -8: "TIMEOUT", -9: "CUDA",
+    -10: "UNSUPPORTED", -11: "NOMEM",
+}
+
+# Every function the header declares; tests check the library exports them.
+EXPORTED = (
+    "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
+    "apc_residual", "apc_solve", "apc_context_info", "apc_last_error", "apc_destroy",
+)
+
+
+class ApcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"APC_ERR_{ERRORS.get(code, code)} ({code}): {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class apc_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("cluster_size", C.c_int32), ("timeout_s", C.c_double)]
+
+
+class apc_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int64), ("sweeps", C.c_int32), ("rel_residual", C.c_double),
+                ("seconds", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libapc.so (built by ``build.build()``); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (run __graft_entry__.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    L.apc_setup.argtypes = [C.POINTER(vp), vp, i64, i64, i64, vp, C.POINTER(i64), i32,
+                            C.POINTER(apc_options), vp]
+    L.apc_optimal_params.argtypes = [dbl, dbl, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl)]
+    L.apc_reset.argtypes = [vp, vp, vp]
+    L.apc_iterate.argtypes = [vp, dbl, dbl, i64, vp]
+    L.apc_get_xbar.argtypes = [vp, vp, vp]
+    L.apc_get_x.argtypes = [vp, vp, i64, vp]
+    L.apc_residual.argtypes = [vp, vp, vp, vp, C.POINTER(dbl), vp]
+    L.apc_solve.argtypes = [vp, dbl, dbl, dbl, i64, i64, i32, vp, C.POINTER(apc_stats), vp]
+    L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
+                                   C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+    L.apc_last_error.argtypes = [vp]
+    L.apc_last_error.restype = C.c_char_p
+    L.apc_destroy.argtypes = [vp]
+    L.apc_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("apc_last_error", "apc_destroy"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check(rc: int, ctx=None):
+    if rc != 0:
+        msg = lib().apc_last_error(ctx).decode(errors="replace")
+        raise ApcError(rc, msg)
+
+
+def apc_optimal_params(mu_min: float, mu_max: float):
+    """Theorem 1's (gamma*, eta*, rho) from the extreme eigenvalues of X."""
+    g, e, r = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().apc_optimal_params(mu_min, mu_max, C.byref(g), C.byref(e), C.byref(r)))
+    return g.value, e.value, r.value
+
+
+class Context:
+    """Owns an ``apc_ctx``; methods mirror the C entry points."""
+
+    def __init__(self, handle: C.c_void_p, device):
+        self.handle = handle
+        self.device = device
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            lib().apc_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> dict:
+        n, N, cb = C.c_int64(), C.c_int64(), C.c_int64()
+        m, w, cs, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().apc_context_info(self.handle, C.byref(n), C.byref(N), C.byref(m), C.byref(w),
+                                      C.byref(cs), C.byref(cl), C.byref(cb)), self.handle)
+        return dict(n=n.value, N=N.value, m=m.value, width=w.value, cluster_size=cs.value,
+                    clusters=cl.value, q_bytes=cb.value)
+
+    def reset(self, rhs=None, stream=None):
+        _check(lib().apc_reset(self.handle, _ptr(rhs), _stream(stream)), self.handle)
+
+    def iterate(self, gamma: float, eta: float, iters: int, stream=None):
+        _check(lib().apc_iterate(self.handle, gamma, eta, int(iters), _stream(stream)), self.handle)
+
+    def xbar(self, out=None, stream=None):
+        import torch
+        info_n = self.info()["n"]
+        out = torch.empty(info_n, dtype=torch.float64, device=self.device) if out is None else out
+        _check(lib().apc_get_xbar(self.handle, _ptr(out), _stream(stream)), self.handle)
+        return out
+
+    def x(self, stream=None):
+        import torch
+        inf = self.info()
+        out = torch.empty((inf["m"], inf["n"]), dtype=torch.float64, device=self.device)
+        _check(lib().apc_get_x(self.handle, _ptr(out), inf["n"], _stream(stream)), self.handle)
+        return out
+
+    def residual(self, x, rhs=None, resid_out=None, stream=None) -> float:
+        rel = C.c_double()
+        _check(lib().apc_residual(self.handle, _ptr(x), _ptr(rhs), _ptr(resid_out), C.byref(rel),
+                                  _stream(stream)), self.handle)
+        return rel.value
+
+    def solve(self, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False,
+              out=None, stream=None, raise_on_error=True):
+        import torch
+        n = self.info()["n"]
+        out = torch.empty(n, dtype=torch.float64, device=self.device) if out is None else out
+        st = apc_stats()
+        rc = lib().apc_solve(self.handle, gamma, eta, tol, int(max_iters), int(check_every), int(bool(refine)),
+                             _ptr(out), C.byref(st), _stream(stream))
+        stats = dict(iterations=st.iterations, sweeps=st.sweeps, rel_residual=st.rel_residual,
+                     seconds=st.seconds, rc=rc)
+        if rc != 0 and raise_on_error:
+            _check(rc, self.handle)
+        return out, stats
+
+
+def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None) -> Context:
+    """Factor the row blocks of A (FP64 CUDA tensor, N x n) for right-hand side b."""
+    import numpy as np
+    import torch
+    if not (A.is_cuda and b.is_cuda) or A.dtype != torch.float64 or b.dtype != torch.float64:
+        raise TypeError("A and b must be float64 CUDA tensors")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major 2-D tensor")
+    b = b.contiguous()
+    offs = np.ascontiguousarray(np.asarray(row_offsets, dtype=np.int64))
+    m = len(offs) - 1
+    opt = apc_options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                      int(cluster_size), float(timeout_s))
+    h = C.c_void_p()
+    with torch.cuda.device(A.device):
+        rc = lib().apc_setup(C.byref(h), _ptr(A), A.shape[0], A.shape[1], A.stride(0), _ptr(b),
+                             offs.ctypes.data_as(C.POINTER(C.c_int64)), m, C.byref(opt), _stream(stream))
+    _check(rc, None)
+    return Context(h, A.device)

@@ -1,0 +1,512 @@
+// C ABI of the APC solver (include/apc.h): context set-up, the solve loop
+// with optional FP64 iterative refinement, and residual checks.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/apc.h"
+#include "apc_internal.h"
+
+using namespace apc;
+
+struct apc_ctx {
+    int device = 0;
+    int precision = APC_F32;
+    int64_t N = 0, n = 0;
+    int m = 0, P = 0, cpl = 0;
+    std::vector<int64_t> offs;
+    int64_t *d_rowstart = nullptr;   // block b starts at row offs[b]
+    int32_t *d_p = nullptr;          // rows per block
+    double *A = nullptr, *b = nullptr, *dinv = nullptr;
+    double *Rinv1 = nullptr, *Rinv2 = nullptr;
+    void *Q = nullptr;
+    void *xw = nullptr, *xbar = nullptr, *zbuf = nullptr;
+    uint32_t *bar = nullptr;
+    int *err = nullptr;
+    double *sums = nullptr, *xtmp = nullptr, *rtmp = nullptr, *xacc = nullptr, *rhs = nullptr;
+    int cs = 1, nw = 1, stages = 2, clusters = 1;
+    int64_t rows_per_cluster = 1;
+    size_t smem = 0;
+    int64_t t = 0;   // global pass counter (z buffer rotation)
+    double timeout_s = 2.0;
+    size_t q_bytes = 0;
+    std::string last_error;
+};
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+int fail(apc_ctx *ctx, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->last_error = buf;
+    else g_setup_error = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                              \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail((ctx), APC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+size_t q_elem_size(int precision) { return precision == APC_F64 ? 8 : (precision == APC_F32 ? 4 : 2); }
+size_t s_elem_size(int precision) { return precision == APC_F64 ? 8 : 4; }
+int state_prec(int precision) { return precision == APC_F64 ? 0 : 1; }
+
+template <typename T>
+int dalloc(apc_ctx *ctx, T **p, size_t bytes) {
+    if (cudaMalloc(reinterpret_cast<void **>(p), bytes ? bytes : 16) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, APC_ERR_NOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    return APC_OK;
+}
+
+void free_all(apc_ctx *c) {
+    void *ps[] = {c->d_rowstart, c->d_p, c->A, c->b, c->dinv, c->Rinv1, c->Rinv2, c->Q, c->xw, c->xbar,
+                  c->zbuf, c->bar, c->err, c->sums, c->xtmp, c->rtmp, c->xacc, c->rhs};
+    for (void *p : ps)
+        if (p) cudaFree(p);
+}
+
+// Pick cluster size, warps per CTA, ring depth and grid for the iteration kernel.
+int configure(apc_ctx *c, int cs_request) {
+    int dev_sms = 0;
+    CK(c, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
+    int smem_optin = 0;
+    CK(c, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const int maxw = c->precision == APC_F64 ? 16 : 32;
+    const int R = iter_rows_per_group(c->precision);
+    const size_t qsz = q_elem_size(c->precision);
+    const int cands[4] = {1, 2, 4, 8};
+    int best = -1;
+    for (int ci = 0; ci < 4; ++ci) {
+        const int cs = cands[ci];
+        if (cs_request > 0 && cs != cs_request) continue;
+        const int nw = (c->m + cs - 1) / cs;
+        if (nw > maxw || (cs - 1) * nw >= c->m) continue;
+        const size_t stage = size_t(R) * nw * c->P * qsz;
+        if (cs_request <= 0 && stage > 64 * 1024 && cs < 8) continue;
+        best = cs;
+        break;
+    }
+    if (best < 0)
+        return fail(c, APC_ERR_UNSUPPORTED, "no cluster size fits m=%d blocks of width %d (requested %d)", c->m, c->P,
+                    cs_request);
+    c->cs = best;
+    c->nw = (c->m + best - 1) / best;
+    const size_t stage = size_t(R) * c->nw * c->P * qsz;
+    const size_t budget = size_t(smem_optin) - 8 * 1024;
+    int64_t clusters = std::max(1, dev_sms / best);
+    clusters = std::min<int64_t>(clusters, (c->n + R - 1) / R);
+    for (int pass = 0; pass < 3; ++pass) {
+        const int64_t rpc = (c->n + clusters - 1) / clusters;
+        const size_t fixed = iter_smem_bytes(c->precision, c->cpl, c->nw, 0, rpc);
+        if (fixed + 2 * stage > budget)
+            return fail(c, APC_ERR_UNSUPPORTED, "shared memory: %zu fixed + 2 x %zu stage bytes exceed %zu", fixed,
+                        stage, budget);
+        int stages = int(std::min<size_t>(4, (budget - fixed) / stage));
+        c->stages = stages;
+        c->rows_per_cluster = rpc;
+        c->smem = iter_smem_bytes(c->precision, c->cpl, c->nw, stages, rpc);
+        const int maxc = iter_max_clusters(c->precision, c->cpl, best, c->nw, c->smem);
+        if (maxc <= 0)
+            return fail(c, APC_ERR_LAUNCH, "no co-resident cluster of %d CTAs x %d threads with %zu B shared memory",
+                        best, c->nw * 32, c->smem);
+        if (maxc >= clusters) break;
+        clusters = maxc;
+    }
+    c->clusters = int(clusters);
+    c->rows_per_cluster = (c->n + clusters - 1) / clusters;
+    c->smem = iter_smem_bytes(c->precision, c->cpl, c->nw, c->stages, c->rows_per_cluster);
+    return APC_OK;
+}
+
+int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
+    const int64_t chunk_max = 1 << 20;
+    while (iters > 0) {
+        const int64_t it = std::min(iters, chunk_max);
+        IterArgs a = {};
+        a.Q = c->Q;
+        a.xw = c->xw;
+        a.xbar = c->xbar;
+        a.zbuf = c->zbuf;
+        a.bar = c->bar;
+        a.err = c->err;
+        a.n = c->n;
+        a.m = c->m;
+        a.P = c->P;
+        a.cs = c->cs;
+        a.nw = c->nw;
+        a.stages = c->stages;
+        a.mode = mode;
+        a.rows_per_cluster = c->rows_per_cluster;
+        a.t0 = c->t;
+        a.iters = it;
+        a.gamma = gamma;
+        a.eta = eta;
+        a.inv_m = 1.0 / c->m;
+        a.timeout_ns = uint64_t(c->timeout_s * 1e9);
+        CK(c, cudaMemsetAsync(c->bar, 0, sizeof(uint32_t), s));
+        cudaError_t e = launch_iter(c->precision, c->cpl, a, c->clusters, c->smem, s);
+        if (e != cudaSuccess) return fail(c, APC_ERR_LAUNCH, "iteration kernel launch failed: %s", cudaGetErrorString(e));
+        c->t += it;
+        iters -= it;
+        int herr = 0;
+        CK(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        if (herr != 0) {
+            cudaMemsetAsync(c->err, 0, sizeof(int), s);
+            cudaStreamSynchronize(s);
+            static const char *what[] = {"", "TMA stage", "cluster exchange", "grid barrier"};
+            return fail(c, APC_ERR_TIMEOUT, "device wait timed out (%s)", what[herr >= 1 && herr <= 3 ? herr : 0]);
+        }
+    }
+    return APC_OK;
+}
+
+int residual(apc_ctx *c, const double *x, const double *rhs, double *out, double *rel, cudaStream_t s) {
+    CK(c, cudaMemsetAsync(c->sums, 0, 2 * sizeof(double), s));
+    CK(c, launch_residual(c->A, c->n, c->N, c->n, x, rhs, out, c->sums, s));
+    double h[2];
+    CK(c, cudaMemcpyAsync(h, c->sums, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    *rel = h[1] > 0 ? std::sqrt(h[0] / h[1]) : std::sqrt(h[0]);
+    return APC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho) {
+    if (!(mu_min > 0.0) || !(mu_min <= mu_max) || !(mu_max <= 1.0 + 1e-12))
+        return fail(nullptr, APC_ERR_INVALID_ARG, "need 0 < mu_min <= mu_max <= 1 (got %g, %g)", mu_min, mu_max);
+    const double smin = std::sqrt(mu_min), smax = std::sqrt(std::min(mu_max, 1.0));
+    const double s = 4.0 / ((smax + smin) * (smax + smin));
+    const double r = (smax - smin) / (smax + smin);
+    const double tr = s + 1.0 - r * r;
+    const double disc = std::max(tr * tr - 4.0 * s, 0.0);
+    if (gamma) *gamma = (tr - std::sqrt(disc)) / 2.0;
+    if (eta) *eta = (tr + std::sqrt(disc)) / 2.0;
+    if (rho) *rho = r;
+    return APC_OK;
+}
+
+int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t lda, const double *b_dev,
+              const int64_t *row_offsets_host, int32_t m, const apc_options *opt, void *stream) {
+    if (!out) return fail(nullptr, APC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A_dev || !b_dev || !row_offsets_host) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL input pointer");
+    if (n < 1 || N < n || lda < n) return fail(nullptr, APC_ERR_INVALID_ARG, "need N >= n >= 1 and lda >= n");
+    if (m < 1 || m > 256) return fail(nullptr, APC_ERR_UNSUPPORTED, "m=%d outside 1..256", m);
+    const int precision = opt ? opt->precision : APC_F32;
+    if (precision < APC_F64 || precision > APC_BF16) return fail(nullptr, APC_ERR_INVALID_ARG, "bad precision");
+    if (row_offsets_host[0] != 0 || row_offsets_host[m] != N)
+        return fail(nullptr, APC_ERR_INVALID_ARG, "row_offsets must start at 0 and end at N");
+    int64_t pmax = 0;
+    for (int i = 0; i < m; ++i) {
+        const int64_t p = row_offsets_host[i + 1] - row_offsets_host[i];
+        if (p < 1) return fail(nullptr, APC_ERR_INVALID_ARG, "block %d is empty or offsets decrease", i);
+        if (p > n) return fail(nullptr, APC_ERR_SINGULAR_BLOCK, "block %d has %lld rows > n", i, (long long)p);
+        pmax = std::max(pmax, p);
+    }
+    if (pmax > 256) return fail(nullptr, APC_ERR_UNSUPPORTED, "block of %lld rows; at most 256", (long long)pmax);
+
+    apc_ctx *c = new apc_ctx();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto bail = [&](int code) {
+        g_setup_error = c->last_error;
+        free_all(c);
+        delete c;
+        return code;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        fail(c, APC_ERR_CUDA, "no CUDA device");
+        return bail(APC_ERR_CUDA);
+    }
+    c->precision = precision;
+    c->N = N;
+    c->n = n;
+    c->m = m;
+    c->P = pmax <= 32 ? 32 : pmax <= 64 ? 64 : pmax <= 128 ? 128 : 256;
+    c->cpl = c->P / 32;
+    c->timeout_s = (opt && opt->timeout_s > 0) ? opt->timeout_s : 2.0;
+    c->offs.assign(row_offsets_host, row_offsets_host + m + 1);
+    const size_t P = c->P;
+    int rc;
+#define ALLOC(ptr, bytes) \
+    if ((rc = dalloc(c, &(ptr), (bytes))) != APC_OK) return bail(rc)
+    ALLOC(c->d_rowstart, sizeof(int64_t) * m);
+    ALLOC(c->d_p, sizeof(int32_t) * m);
+    ALLOC(c->A, sizeof(double) * N * n);
+    ALLOC(c->b, sizeof(double) * N);
+    ALLOC(c->dinv, sizeof(double) * N);
+    ALLOC(c->Rinv1, sizeof(double) * m * P * P);
+    ALLOC(c->Rinv2, sizeof(double) * m * P * P);
+    ALLOC(c->err, sizeof(int) * 4);
+    ALLOC(c->bar, sizeof(uint32_t) * 4);
+    ALLOC(c->sums, sizeof(double) * 4);
+    ALLOC(c->xtmp, sizeof(double) * n);
+    ALLOC(c->xacc, sizeof(double) * n);
+    ALLOC(c->rtmp, sizeof(double) * N);
+    ALLOC(c->rhs, sizeof(double) * N);
+    std::vector<int64_t> rs(m);
+    std::vector<int32_t> pc(m);
+    for (int i = 0; i < m; ++i) {
+        rs[i] = row_offsets_host[i];
+        pc[i] = int32_t(row_offsets_host[i + 1] - row_offsets_host[i]);
+    }
+#define CKB(call)                                                                              \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            fail(c, APC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));             \
+            return bail(APC_ERR_CUDA);                                                         \
+        }                                                                                      \
+    } while (0)
+    CKB(cudaMemcpyAsync(c->d_rowstart, rs.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    CKB(cudaMemcpyAsync(c->d_p, pc.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, s));
+    CKB(cudaMemcpy2DAsync(c->A, sizeof(double) * n, A_dev, sizeof(double) * lda, sizeof(double) * n, N,
+                          cudaMemcpyDeviceToDevice, s));
+    CKB(cudaMemcpyAsync(c->b, b_dev, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    CKB(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
+
+    // non-finite inputs
+    CKB(launch_check_finite(c->A, N * n, c->err + 1, s));
+    CKB(launch_check_finite(c->b, N, c->err + 1, s));
+    CKB(launch_rownorm(c->A, n, N, n, c->dinv, c->err, s));
+    int herr[4];
+    CKB(cudaMemcpyAsync(herr, c->err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    CKB(cudaStreamSynchronize(s));
+    if (herr[1]) {
+        fail(c, APC_ERR_NONFINITE, "A or b holds NaN or Inf");
+        return bail(APC_ERR_NONFINITE);
+    }
+    if (herr[0]) {
+        fail(c, APC_ERR_SINGULAR_BLOCK, "A has a zero row");
+        return bail(APC_ERR_SINGULAR_BLOCK);
+    }
+
+    // two passes of Cholesky QR in FP64 (scratch freed at the end)
+    double *G = nullptr, *QT1 = nullptr, *QT2 = nullptr;
+    int64_t *rs2 = nullptr;
+    auto free_scratch = [&]() {
+        if (G) cudaFree(G);
+        if (QT1) cudaFree(QT1);
+        if (QT2) cudaFree(QT2);
+        if (rs2) cudaFree(rs2);
+    };
+    auto bail2 = [&](int code) {
+        free_scratch();
+        return bail(code);
+    };
+    if (dalloc(c, &G, sizeof(double) * m * P * P) || dalloc(c, &QT1, sizeof(double) * m * P * n) ||
+        dalloc(c, &QT2, sizeof(double) * m * P * n) || dalloc(c, &rs2, sizeof(int64_t) * m))
+        return bail2(APC_ERR_NOMEM);
+    for (int i = 0; i < m; ++i) rs[i] = int64_t(i) * P;
+#define CKB2(call)                                                                             \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            fail(c, APC_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));             \
+            return bail2(APC_ERR_CUDA);                                                        \
+        }                                                                                      \
+    } while (0)
+    CKB2(cudaMemcpyAsync(rs2, rs.data(), sizeof(int64_t) * m, cudaMemcpyHostToDevice, s));
+    CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
+    CKB2(launch_gram(c->A, n, c->d_rowstart, c->d_p, c->dinv, m, int(P), n, G, s));
+    CKB2(launch_chol(G, c->Rinv1, c->d_p, m, int(P), 1e-14, c->err + 2, s));
+    CKB2(launch_qt(c->A, n, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, m, int(P), n, QT1, s));
+    CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
+    CKB2(launch_gram(QT1, n, rs2, c->d_p, nullptr, m, int(P), n, G, s));
+    CKB2(launch_chol(G, c->Rinv2, c->d_p, m, int(P), 1e-14, c->err + 3, s));
+    CKB2(launch_qt(QT1, n, rs2, c->d_p, nullptr, c->Rinv2, m, int(P), n, QT2, s));
+    c->q_bytes = size_t(n) * m * P * q_elem_size(precision);
+    if (dalloc(c, &c->Q, c->q_bytes)) return bail2(APC_ERR_NOMEM);
+    CKB2(launch_pack(QT2, m, int(P), n, precision, c->Q, s));
+    CKB2(cudaMemcpyAsync(herr, c->err, sizeof(herr), cudaMemcpyDeviceToHost, s));
+    CKB2(cudaStreamSynchronize(s));
+    free_scratch();
+    G = QT1 = QT2 = nullptr;
+    rs2 = nullptr;
+    if (herr[2] || herr[3]) {
+        const int blk = (herr[2] ? herr[2] : herr[3]) - 1;
+        fail(c, APC_ERR_SINGULAR_BLOCK, "block %d: A_i A_i^T is numerically singular (Cholesky pivot)", blk);
+        return bail(APC_ERR_SINGULAR_BLOCK);
+    }
+
+    const size_t ssz = s_elem_size(precision);
+    ALLOC(c->xw, ssz * n * m);
+    ALLOC(c->xbar, ssz * n);
+    ALLOC(c->zbuf, ssz * 3 * m * P);
+    CKB(cudaMemsetAsync(c->xw, 0, ssz * n * m, s));
+    CKB(cudaMemsetAsync(c->xbar, 0, ssz * n, s));
+    CKB(cudaMemsetAsync(c->zbuf, 0, ssz * 3 * m * P, s));
+    CKB(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
+    if ((rc = configure(c, opt ? opt->cluster_size : 0)) != APC_OK) return bail(rc);
+    CKB(cudaStreamSynchronize(s));
+    *out = c;
+    return APC_OK;
+#undef ALLOC
+#undef CKB
+#undef CKB2
+}
+
+int apc_reset(apc_ctx *c, const double *rhs_dev, void *stream) {
+    if (!c) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL context");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ssz = s_elem_size(c->precision);
+    const double *rhs = rhs_dev ? rhs_dev : c->b;
+    CK(c, cudaMemsetAsync(c->zbuf, 0, ssz * 3 * c->m * c->P, s));
+    CK(c, cudaMemsetAsync(c->xbar, 0, ssz * c->n, s));
+    CK(c, launch_csolve(rhs, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P,
+                        state_prec(c->precision), c->zbuf, s));
+    c->t = 0;
+    return run_pass(c, MODE_INIT, 1.0, 1.0, 1, s);
+}
+
+int apc_iterate(apc_ctx *c, double gamma, double eta, int64_t iters, void *stream) {
+    if (!c) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL context");
+    if (!(gamma > 0.0 && gamma < 2.0) || !std::isfinite(eta))
+        return fail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2) and eta must be finite", gamma);
+    if (iters < 0) return fail(c, APC_ERR_INVALID_ARG, "iters < 0");
+    if (iters == 0) return APC_OK;
+    if (c->t == 0) return fail(c, APC_ERR_INVALID_ARG, "apc_reset must precede apc_iterate");
+    return run_pass(c, MODE_APC, gamma, eta, iters, static_cast<cudaStream_t>(stream));
+}
+
+int apc_get_xbar(apc_ctx *c, double *x_dev, void *stream) {
+    if (!c || !x_dev) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, static_cast<cudaStream_t>(stream)));
+    return APC_OK;
+}
+
+int apc_get_x(apc_ctx *c, double *x_dev, int64_t ldx, void *stream) {
+    if (!c || !x_dev || ldx < c->n) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
+    CK(c, launch_unpack_x(c->xw, state_prec(c->precision), c->n, c->m, x_dev, ldx, static_cast<cudaStream_t>(stream)));
+    return APC_OK;
+}
+
+int apc_residual(apc_ctx *c, const double *x_dev, const double *rhs_dev, double *resid_dev, double *rel_host,
+                 void *stream) {
+    if (!c || !x_dev || !rel_host) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    return residual(c, x_dev, rhs_dev ? rhs_dev : c->b, resid_dev ? resid_dev : c->rtmp, rel_host,
+                    static_cast<cudaStream_t>(stream));
+}
+
+int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iters, int64_t check_every,
+              int32_t refine, double *x_dev, apc_stats *stats, void *stream) {
+    if (!c || !x_dev) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    if (!(gamma > 0.0 && gamma < 2.0)) return fail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2)", gamma);
+    if (check_every <= 0) check_every = 100;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const auto t_start = std::chrono::steady_clock::now();
+    int64_t iters = 0;
+    int sweeps = 0;
+    double rel = 0.0;
+    int rc = APC_OK;
+    if (!refine) {
+        sweeps = 1;
+        if ((rc = apc_reset(c, nullptr, s)) != APC_OK) return rc;
+        CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, s));
+        if ((rc = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return rc;
+        const double rel0 = rel;
+        rc = APC_ERR_NOT_CONVERGED;
+        while (iters < max_iters) {
+            if (rel <= tol) { rc = APC_OK; break; }
+            const int64_t k = std::min(check_every, max_iters - iters);
+            int r2 = run_pass(c, MODE_APC, gamma, eta, k, s);
+            if (r2 != APC_OK) return r2;
+            iters += k;
+            CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, s));
+            if ((r2 = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return r2;
+            if (!std::isfinite(rel)) { rc = fail(c, APC_ERR_NONFINITE, "iterate became non-finite"); break; }
+            if (rel > 1e8 * std::max(rel0, 1e-300)) { rc = fail(c, APC_ERR_DIVERGED, "residual grew to %g", rel); break; }
+        }
+        if (rc == APC_OK || rc == APC_ERR_NOT_CONVERGED) {
+            if (rel <= tol) rc = APC_OK;
+            else fail(c, APC_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %lld iterations", rel, tol,
+                      (long long)iters);
+        }
+    } else {
+        // FP64 iterative refinement: x <- x + delta, A delta ~= r = b - A x by APC
+        CK(c, cudaMemsetAsync(c->xacc, 0, sizeof(double) * c->n, s));
+        CK(c, cudaMemcpyAsync(c->rhs, c->b, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, s));
+        if ((rc = residual(c, c->xacc, c->b, c->rhs, &rel, s)) != APC_OK) return rc;
+        rc = APC_ERR_NOT_CONVERGED;
+        const int max_sweeps = 64;
+        while (iters < max_iters && sweeps < max_sweeps) {
+            if (rel <= tol) { rc = APC_OK; break; }
+            ++sweeps;
+            int r2 = apc_reset(c, c->rhs, s);
+            if (r2 != APC_OK) return r2;
+            double best = 1.0, prev = 1.0, inner = 1.0;
+            // inner APC on A delta = r; stop when its residual stagnates
+            while (iters < max_iters) {
+                const int64_t k = std::min(check_every, max_iters - iters);
+                if ((r2 = run_pass(c, MODE_APC, gamma, eta, k, s)) != APC_OK) return r2;
+                iters += k;
+                CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, c->xtmp, s));
+                if ((r2 = residual(c, c->xtmp, c->rhs, c->rtmp, &inner, s)) != APC_OK) return r2;
+                if (!std::isfinite(inner)) return fail(c, APC_ERR_NONFINITE, "inner iterate became non-finite");
+                if (inner > 1e8) return fail(c, APC_ERR_DIVERGED, "inner residual grew to %g", inner);
+                const bool stalled = inner > 0.9 * prev && inner < 0.5;
+                prev = inner;
+                best = std::min(best, inner);
+                if (inner <= 1e-4 || stalled || rel * inner <= 0.5 * tol) break;
+            }
+            CK(c, launch_axpy_f64(c->xacc, c->xtmp, 1.0, c->n, s));
+            if ((r2 = residual(c, c->xacc, c->b, c->rhs, &rel, s)) != APC_OK) return r2;
+            if (!std::isfinite(rel)) return fail(c, APC_ERR_NONFINITE, "refined iterate became non-finite");
+            (void)best;
+        }
+        CK(c, cudaMemcpyAsync(x_dev, c->xacc, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaStreamSynchronize(s));
+        if (rel <= tol) rc = APC_OK;
+        else rc = fail(c, APC_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %d sweeps", rel, tol, sweeps);
+    }
+    if (stats) {
+        stats->iterations = iters;
+        stats->sweeps = sweeps;
+        stats->rel_residual = rel;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    }
+    return rc;
+}
+
+int apc_context_info(const apc_ctx *c, int64_t *n, int64_t *N, int32_t *m, int32_t *width, int32_t *cluster_size,
+                     int32_t *clusters, int64_t *q_bytes) {
+    if (!c) return APC_ERR_INVALID_ARG;
+    if (n) *n = c->n;
+    if (N) *N = c->N;
+    if (m) *m = c->m;
+    if (width) *width = c->P;
+    if (cluster_size) *cluster_size = c->cs;
+    if (clusters) *clusters = c->clusters;
+    if (q_bytes) *q_bytes = int64_t(c->q_bytes);
+    return APC_OK;
+}
+
+const char *apc_last_error(const apc_ctx *c) { return c ? c->last_error.c_str() : g_setup_error.c_str(); }
+
+void apc_destroy(apc_ctx *c) {
+    if (!c) return;
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"
