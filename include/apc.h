@@ -59,6 +59,7 @@ typedef struct apc_ctx apc_ctx;
 typedef struct apc_options {
     int32_t precision;      /* APC_F64 / APC_F32 / APC_BF16                   */
     int32_t cluster_size;   /* CTAs sharing one row range; 0 = automatic      */
+    int32_t workers_per_warp; /* 1 or 2 blocks per warp; 0 = automatic        */
     double  timeout_s;      /* limit of every device-side wait; 0 = 2 s       */
 } apc_options;
 
@@ -112,6 +113,12 @@ int apc_get_xbar(apc_ctx *ctx, double *x_dev, void *stream);
 /* apc_get_x -- copy the machines' iterates x_i (m x n, row i = x_i, FP64,
  * device, leading dimension ldx >= n) to x_dev.  For tests and checkpoints. */
 int apc_get_x(apc_ctx *ctx, double *x_dev, int64_t ldx, void *stream);
+
+/* apc_get_basis -- copy the orthonormal basis Q_i of block i (Sec. 3.3; the
+ * columns span the row space of A_i, so P_i = I - Q_i Q_i^T) to Q_dev as an
+ * n x p_i FP64 row-major matrix with leading dimension ldq >= p_i.  The
+ * values are those the iteration uses (after rounding to its precision). */
+int apc_get_basis(apc_ctx *ctx, int32_t block, double *Q_dev, int64_t ldq, void *stream);
 
 /* apc_residual -- FP64 relative residual ||r - A x||_2 / ||r||_2 of x_dev
  * (FP64, n, device) against rhs_dev (NULL = the stored b).  If resid_dev is

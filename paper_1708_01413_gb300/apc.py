@@ -25,7 +25,7 @@ ERRORS = {
 # Every function the header declares; tests check the library exports them.
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
-    "apc_residual", "apc_solve", "apc_context_info", "apc_last_error", "apc_destroy",
+    "apc_get_basis", "apc_residual", "apc_solve", "apc_context_info", "apc_last_error", "apc_destroy",
 )
 
 
@@ -37,7 +37,8 @@ class ApcError(RuntimeError):
 
 
 class apc_options(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("cluster_size", C.c_int32), ("timeout_s", C.c_double)]
+    _fields_ = [("precision", C.c_int32), ("cluster_size", C.c_int32), ("workers_per_warp", C.c_int32),
+                ("timeout_s", C.c_double)]
 
 
 class apc_stats(C.Structure):
@@ -64,6 +65,7 @@ def lib() -> C.CDLL:
     L.apc_iterate.argtypes = [vp, dbl, dbl, i64, vp]
     L.apc_get_xbar.argtypes = [vp, vp, vp]
     L.apc_get_x.argtypes = [vp, vp, i64, vp]
+    L.apc_get_basis.argtypes = [vp, i32, vp, i64, vp]
     L.apc_residual.argtypes = [vp, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_solve.argtypes = [vp, dbl, dbl, dbl, i64, i64, i32, vp, C.POINTER(apc_stats), vp]
     L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
@@ -105,9 +107,10 @@ def apc_optimal_params(mu_min: float, mu_max: float):
 class Context:
     """Owns an ``apc_ctx``; methods mirror the C entry points."""
 
-    def __init__(self, handle: C.c_void_p, device):
+    def __init__(self, handle: C.c_void_p, device, offsets=None):
         self.handle = handle
         self.device = device
+        self._offs = offsets
 
     def __del__(self):
         try:
@@ -148,6 +151,15 @@ class Context:
         _check(lib().apc_get_x(self.handle, _ptr(out), inf["n"], _stream(stream)), self.handle)
         return out
 
+    def basis(self, block: int, stream=None):
+        """Q_i of block ``block`` as an n x p_i FP64 tensor."""
+        import torch
+        inf = self.info()
+        p = int(self._offs[block + 1] - self._offs[block])
+        out = torch.empty((inf["n"], p), dtype=torch.float64, device=self.device)
+        _check(lib().apc_get_basis(self.handle, int(block), _ptr(out), p, _stream(stream)), self.handle)
+        return out
+
     def residual(self, x, rhs=None, resid_out=None, stream=None) -> float:
         rel = C.c_double()
         _check(lib().apc_residual(self.handle, _ptr(x), _ptr(rhs), _ptr(resid_out), C.byref(rel),
@@ -169,7 +181,8 @@ class Context:
         return out, stats
 
 
-def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None) -> Context:
+def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,
+              workers_per_warp=0) -> Context:
     """Factor the row blocks of A (FP64 CUDA tensor, N x n) for right-hand side b."""
     import numpy as np
     import torch
@@ -181,10 +194,10 @@ def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0,
     offs = np.ascontiguousarray(np.asarray(row_offsets, dtype=np.int64))
     m = len(offs) - 1
     opt = apc_options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                      int(cluster_size), float(timeout_s))
+                      int(cluster_size), int(workers_per_warp), float(timeout_s))
     h = C.c_void_p()
     with torch.cuda.device(A.device):
         rc = lib().apc_setup(C.byref(h), _ptr(A), A.shape[0], A.shape[1], A.stride(0), _ptr(b),
                              offs.ctypes.data_as(C.POINTER(C.c_int64)), m, C.byref(opt), _stream(stream))
     _check(rc, None)
-    return Context(h, A.device)
+    return Context(h, A.device, offs)

@@ -25,11 +25,12 @@ struct apc_ctx {
     double *A = nullptr, *b = nullptr, *dinv = nullptr;
     double *Rinv1 = nullptr, *Rinv2 = nullptr;
     void *Q = nullptr;
-    void *xw = nullptr, *xbar = nullptr, *zbuf = nullptr;
+    void *xw = nullptr, *zbuf = nullptr;
+    double *xbar = nullptr;  // master estimate, FP64 in every mode
     uint32_t *bar = nullptr;
     int *err = nullptr;
     double *sums = nullptr, *xtmp = nullptr, *rtmp = nullptr, *xacc = nullptr, *rhs = nullptr;
-    int cs = 1, nw = 1, stages = 2, clusters = 1;
+    int cs = 1, nw = 1, wpw = 1, stages = 2, clusters = 1;
     int64_t rows_per_cluster = 1;
     size_t smem = 0;
     int64_t t = 0;   // global pass counter (z buffer rotation)
@@ -81,47 +82,56 @@ void free_all(apc_ctx *c) {
         if (p) cudaFree(p);
 }
 
-// Pick cluster size, warps per CTA, ring depth and grid for the iteration kernel.
-int configure(apc_ctx *c, int cs_request) {
+// Pick cluster size, workers per warp, warps per CTA, ring depth and grid for
+// the iteration kernel.  Every CTA of a cluster gets W = ceil(m / cs) worker
+// slots; a stage holds R rows of W * P elements of Q.
+int configure(apc_ctx *c, int cs_request, int wpw_request) {
     int dev_sms = 0;
     CK(c, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int smem_optin = 0;
     CK(c, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    const int maxw = c->precision == APC_F64 ? 16 : 32;
-    const int R = iter_rows_per_group(c->precision);
+    const int R = kRowsPerGroup;
     const size_t qsz = q_elem_size(c->precision);
+    const size_t budget = size_t(smem_optin) - 4 * 1024;
     const int cands[4] = {1, 2, 4, 8};
-    int best = -1;
-    for (int ci = 0; ci < 4; ++ci) {
+    int best = -1, best_wpw = 0, best_nw = 0, best_stages = 0;
+    for (int ci = 0; ci < 4 && best < 0; ++ci) {
         const int cs = cands[ci];
         if (cs_request > 0 && cs != cs_request) continue;
-        const int nw = (c->m + cs - 1) / cs;
-        if (nw > maxw || (cs - 1) * nw >= c->m) continue;
-        const size_t stage = size_t(R) * nw * c->P * qsz;
-        if (cs_request <= 0 && stage > 64 * 1024 && cs < 8) continue;
+        const int W0 = (c->m + cs - 1) / cs;
+        const int wpw = wpw_request > 0 ? wpw_request : (W0 >= 2 ? 2 : 1);
+        if (wpw < 1 || wpw > 2) continue;
+        const int nw = (W0 + wpw - 1) / wpw;
+        const int W = nw * wpw;  // worker slots per CTA
+        if (W > 32 || nw > kMaxElemWarps || (cs - 1) * W >= c->m) continue;
+        const size_t stage = size_t(R) * W * c->P * qsz;
+        const int64_t rpc_guess = (c->n + std::max(1, dev_sms / cs) - 1) / std::max(1, dev_sms / cs);
+        const size_t fixed = iter_smem_bytes(c->precision, c->P, W, 0, rpc_guess) + 1024;
+        if (fixed >= budget) continue;
+        const int stages = int(std::min<size_t>(6, (budget - fixed) / stage));
+        const int min_stages = kMinStages;
+        if (stages < min_stages) continue;
         best = cs;
-        break;
+        best_wpw = wpw;
+        best_nw = nw;
+        best_stages = stages;
     }
     if (best < 0)
-        return fail(c, APC_ERR_UNSUPPORTED, "no cluster size fits m=%d blocks of width %d (requested %d)", c->m, c->P,
-                    cs_request);
+        return fail(c, APC_ERR_UNSUPPORTED, "no cluster size fits m=%d blocks of width %d (requested cs=%d wpw=%d)",
+                    c->m, c->P, cs_request, wpw_request);
     c->cs = best;
-    c->nw = (c->m + best - 1) / best;
-    const size_t stage = size_t(R) * c->nw * c->P * qsz;
-    const size_t budget = size_t(smem_optin) - 8 * 1024;
+    c->wpw = best_wpw;
+    c->nw = best_nw;
+    c->stages = best_stages;
+    const int W = c->nw * c->wpw;
     int64_t clusters = std::max(1, dev_sms / best);
     clusters = std::min<int64_t>(clusters, (c->n + R - 1) / R);
     for (int pass = 0; pass < 3; ++pass) {
-        const int64_t rpc = (c->n + clusters - 1) / clusters;
-        const size_t fixed = iter_smem_bytes(c->precision, c->cpl, c->nw, 0, rpc);
-        if (fixed + 2 * stage > budget)
-            return fail(c, APC_ERR_UNSUPPORTED, "shared memory: %zu fixed + 2 x %zu stage bytes exceed %zu", fixed,
-                        stage, budget);
-        int stages = int(std::min<size_t>(4, (budget - fixed) / stage));
-        c->stages = stages;
-        c->rows_per_cluster = rpc;
-        c->smem = iter_smem_bytes(c->precision, c->cpl, c->nw, stages, rpc);
-        const int maxc = iter_max_clusters(c->precision, c->cpl, best, c->nw, c->smem);
+        c->rows_per_cluster = (c->n + clusters - 1) / clusters;
+        c->smem = iter_smem_bytes(c->precision, c->P, W, c->stages, c->rows_per_cluster);
+        if (c->smem > budget)
+            return fail(c, APC_ERR_UNSUPPORTED, "shared memory %zu exceeds %zu", c->smem, budget);
+        const int maxc = iter_max_clusters(c->precision, c->cpl, c->wpw, best, c->nw, c->smem);
         if (maxc <= 0)
             return fail(c, APC_ERR_LAUNCH, "no co-resident cluster of %d CTAs x %d threads with %zu B shared memory",
                         best, c->nw * 32, c->smem);
@@ -130,7 +140,7 @@ int configure(apc_ctx *c, int cs_request) {
     }
     c->clusters = int(clusters);
     c->rows_per_cluster = (c->n + clusters - 1) / clusters;
-    c->smem = iter_smem_bytes(c->precision, c->cpl, c->nw, c->stages, c->rows_per_cluster);
+    c->smem = iter_smem_bytes(c->precision, c->P, W, c->stages, c->rows_per_cluster);
     return APC_OK;
 }
 
@@ -150,6 +160,7 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         a.P = c->P;
         a.cs = c->cs;
         a.nw = c->nw;
+        a.wpw = c->wpw;
         a.stages = c->stages;
         a.mode = mode;
         a.rows_per_cluster = c->rows_per_cluster;
@@ -242,7 +253,7 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     c->N = N;
     c->n = n;
     c->m = m;
-    c->P = pmax <= 32 ? 32 : pmax <= 64 ? 64 : pmax <= 128 ? 128 : 256;
+    c->P = pmax <= 64 ? 64 : pmax <= 128 ? 128 : 256;
     c->cpl = c->P / 32;
     c->timeout_s = (opt && opt->timeout_s > 0) ? opt->timeout_s : 2.0;
     c->offs.assign(row_offsets_host, row_offsets_host + m + 1);
@@ -351,13 +362,13 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
 
     const size_t ssz = s_elem_size(precision);
     ALLOC(c->xw, ssz * n * m);
-    ALLOC(c->xbar, ssz * n);
+    ALLOC(c->xbar, sizeof(double) * n);
     ALLOC(c->zbuf, ssz * 3 * m * P);
     CKB(cudaMemsetAsync(c->xw, 0, ssz * n * m, s));
-    CKB(cudaMemsetAsync(c->xbar, 0, ssz * n, s));
+    CKB(cudaMemsetAsync(c->xbar, 0, sizeof(double) * n, s));
     CKB(cudaMemsetAsync(c->zbuf, 0, ssz * 3 * m * P, s));
     CKB(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
-    if ((rc = configure(c, opt ? opt->cluster_size : 0)) != APC_OK) return bail(rc);
+    if ((rc = configure(c, opt ? opt->cluster_size : 0, opt ? opt->workers_per_warp : 0)) != APC_OK) return bail(rc);
     CKB(cudaStreamSynchronize(s));
     *out = c;
     return APC_OK;
@@ -372,7 +383,7 @@ int apc_reset(apc_ctx *c, const double *rhs_dev, void *stream) {
     const size_t ssz = s_elem_size(c->precision);
     const double *rhs = rhs_dev ? rhs_dev : c->b;
     CK(c, cudaMemsetAsync(c->zbuf, 0, ssz * 3 * c->m * c->P, s));
-    CK(c, cudaMemsetAsync(c->xbar, 0, ssz * c->n, s));
+    CK(c, cudaMemsetAsync(c->xbar, 0, sizeof(double) * c->n, s));
     CK(c, launch_csolve(rhs, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P,
                         state_prec(c->precision), c->zbuf, s));
     c->t = 0;
@@ -391,13 +402,22 @@ int apc_iterate(apc_ctx *c, double gamma, double eta, int64_t iters, void *strea
 
 int apc_get_xbar(apc_ctx *c, double *x_dev, void *stream) {
     if (!c || !x_dev) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
-    CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, static_cast<cudaStream_t>(stream)));
+    CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
     return APC_OK;
 }
 
 int apc_get_x(apc_ctx *c, double *x_dev, int64_t ldx, void *stream) {
     if (!c || !x_dev || ldx < c->n) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
     CK(c, launch_unpack_x(c->xw, state_prec(c->precision), c->n, c->m, x_dev, ldx, static_cast<cudaStream_t>(stream)));
+    return APC_OK;
+}
+
+int apc_get_basis(apc_ctx *c, int32_t block, double *Q_dev, int64_t ldq, void *stream) {
+    if (!c || !Q_dev || block < 0 || block >= c->m) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
+    const int p = int(c->offs[block + 1] - c->offs[block]);
+    if (ldq < p) return fail(c, APC_ERR_INVALID_ARG, "ldq < p_i");
+    CK(c, launch_get_basis(c->Q, c->precision, c->n, c->m, c->P, block, p, Q_dev, ldq,
+                           static_cast<cudaStream_t>(stream)));
     return APC_OK;
 }
 
@@ -422,7 +442,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
     if (!refine) {
         sweeps = 1;
         if ((rc = apc_reset(c, nullptr, s)) != APC_OK) return rc;
-        CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, s));
+        CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
         if ((rc = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return rc;
         const double rel0 = rel;
         rc = APC_ERR_NOT_CONVERGED;
@@ -432,7 +452,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
             int r2 = run_pass(c, MODE_APC, gamma, eta, k, s);
             if (r2 != APC_OK) return r2;
             iters += k;
-            CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, x_dev, s));
+            CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
             if ((r2 = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return r2;
             if (!std::isfinite(rel)) { rc = fail(c, APC_ERR_NONFINITE, "iterate became non-finite"); break; }
             if (rel > 1e8 * std::max(rel0, 1e-300)) { rc = fail(c, APC_ERR_DIVERGED, "residual grew to %g", rel); break; }
@@ -460,7 +480,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
                 const int64_t k = std::min(check_every, max_iters - iters);
                 if ((r2 = run_pass(c, MODE_APC, gamma, eta, k, s)) != APC_OK) return r2;
                 iters += k;
-                CK(c, launch_to_f64(c->xbar, state_prec(c->precision), c->n, c->xtmp, s));
+                CK(c, cudaMemcpyAsync(c->xtmp, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
                 if ((r2 = residual(c, c->xtmp, c->rhs, c->rtmp, &inner, s)) != APC_OK) return r2;
                 if (!std::isfinite(inner)) return fail(c, APC_ERR_NONFINITE, "inner iterate became non-finite");
                 if (inner > 1e8) return fail(c, APC_ERR_DIVERGED, "inner residual grew to %g", inner);

@@ -19,14 +19,15 @@ enum PassMode : int {
 struct IterArgs {
     const void *Q;      // [n][m][P] in the iteration precision
     void *xw;           // [n][m] machines' iterates (TS)
-    void *xbar;         // [n] master estimate (TS)
+    double *xbar;       // [n] master estimate (always FP64)
     void *zbuf;         // 3 x [m][P] (TS): z_i = Q_i^T(...) for the next pass
     uint32_t *bar;      // grid barrier counter (zeroed before each launch)
     int *err;           // device error word (0 = ok)
     int64_t n;
     int32_t m, P;
     int32_t cs;         // cluster size (CTAs sharing a row range)
-    int32_t nw;         // workers (warps) per CTA
+    int32_t nw;         // warps per CTA
+    int32_t wpw;        // workers per warp (1 or 2); worker slots per CTA = nw * wpw
     int32_t stages;     // TMA ring depth
     int32_t mode;
     int64_t rows_per_cluster;
@@ -43,11 +44,21 @@ enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_XCHG = 2, DEV_T
 // error; `clusters` is the grid size in clusters (all co-resident).
 cudaError_t launch_iter(int precision, int cpl, const IterArgs &a, int clusters, size_t smem,
                         cudaStream_t s);
-// Maximum number of co-resident clusters for a configuration (0 on failure)
-// and the dynamic shared memory size it needs.
-int iter_max_clusters(int precision, int cpl, int cs, int nw, size_t smem);
-size_t iter_smem_bytes(int precision, int cpl, int nw, int stages, int64_t rows_per_cluster);
-int iter_rows_per_group(int precision);
+// Maximum number of co-resident clusters for a configuration (0 on failure).
+int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t smem);
+// Minimum ring depth: three stages are in use at a time.
+constexpr int kMinStages = 4;
+// Dynamic shared memory of one CTA: `slots` worker slots, `stages` ring stages.
+size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster);
+constexpr int kRowsPerGroup = 2;   // rows of Q per pipeline step
+constexpr int kMaxElemWarps = 16;  // warps streaming Q per CTA of the iteration kernel
+constexpr int kCtlWarps = 2;       // control warps per CTA (one per row of a group)
+constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps) * 32;
+
+// Kernel entry points, one translation unit per Q precision.
+void *iter_kernel_f64(int cpl, int wpw, bool apc);
+void *iter_kernel_f32(int cpl, int wpw, bool apc);
+void *iter_kernel_bf16(int cpl, int wpw, bool apc);
 
 // ---- setup (FP64) -----------------------------------------------------------
 cudaError_t launch_rownorm(const double *A, int64_t lda, int64_t N, int64_t n, double *dinv, int *err,
@@ -83,6 +94,9 @@ cudaError_t launch_from_f64(const double *src, int precision, int64_t count, voi
 // x_i rows of the [n][m] state into an m x n FP64 matrix (ld >= n).
 cudaError_t launch_unpack_x(const void *xw, int precision, int64_t n, int m, double *out, int64_t ld,
                             cudaStream_t s);
+// out[j*ldq + c] = Q[j][b][c] for c < p (FP64), one block b.
+cudaError_t launch_get_basis(const void *Q, int precision, int64_t n, int m, int P, int b, int p, double *out,
+                             int64_t ldq, cudaStream_t s);
 cudaError_t launch_axpy_f64(double *y, const double *x, double a, int64_t count, cudaStream_t s);
 // flags[0] |= 1 if any of v[0..count) is not finite.
 cudaError_t launch_check_finite(const double *v, int64_t count, int *flag, cudaStream_t s);

@@ -1,0 +1,6 @@
+// Instantiations of the persistent iteration kernel for Q stored as __nv_bfloat16.
+#include "apc_iter_impl.cuh"
+
+namespace apc {
+void *iter_kernel_bf16(int cpl, int wpw, bool apc) { return iterk::kernel_for<__nv_bfloat16, float>(cpl, wpw, apc); }
+}  // namespace apc

@@ -1,0 +1,6 @@
+// Instantiations of the persistent iteration kernel for Q stored as double.
+#include "apc_iter_impl.cuh"
+
+namespace apc {
+void *iter_kernel_f64(int cpl, int wpw, bool apc) { return iterk::kernel_for<double, double>(cpl, wpw, apc); }
+}  // namespace apc

@@ -114,6 +114,11 @@ __device__ __forceinline__ void st_async_f64(uint32_t remote_addr, double v, uin
                  ::"r"(remote_addr), "l"(__double_as_longlong(v)), "r"(remote_bar) : "memory");
 }
 
+__device__ __forceinline__ void st_async_b64(uint32_t remote_addr, uint64_t v, uint32_t remote_bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 ::"r"(remote_addr), "l"(v), "r"(remote_bar) : "memory");
+}
+
 // ---- global acquire/release ------------------------------------------------
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;

@@ -348,6 +348,27 @@ __global__ void unpack_x_kernel(const TS *xw, int64_t n, int m, double *out, int
     }
 }
 
+template <typename TQ>
+__global__ void get_basis_kernel(const TQ *Q, int64_t n, int m, int P, int b, int p, double *out, int64_t ldq) {
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n * p;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = idx / p;
+        const int c = int(idx % p);
+        out[j * ldq + c] = double(Q[(size_t(j) * m + b) * P + c]);
+    }
+}
+
+template <>
+__global__ void get_basis_kernel<__nv_bfloat16>(const __nv_bfloat16 *Q, int64_t n, int m, int P, int b, int p,
+                                                double *out, int64_t ldq) {
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < n * p;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = idx / p;
+        const int c = int(idx % p);
+        out[j * ldq + c] = double(__bfloat162float(Q[(size_t(j) * m + b) * P + c]));
+    }
+}
+
 __global__ void axpy_kernel(double *y, const double *x, double a, int64_t count) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
         y[i] = fma(a, x[i], y[i]);
@@ -457,6 +478,19 @@ cudaError_t launch_unpack_x(const void *xw, int precision, int64_t n, int m, dou
         unpack_x_kernel<double><<<grid1d(n * m, 256), 256, 0, s>>>(static_cast<const double *>(xw), n, m, out, ld);
     else
         unpack_x_kernel<float><<<grid1d(n * m, 256), 256, 0, s>>>(static_cast<const float *>(xw), n, m, out, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_basis(const void *Q, int precision, int64_t n, int m, int P, int b, int p, double *out,
+                             int64_t ldq, cudaStream_t s) {
+    const unsigned g = grid1d(n * p, 256);
+    if (precision == 0)
+        get_basis_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(Q), n, m, P, b, p, out, ldq);
+    else if (precision == 1)
+        get_basis_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(Q), n, m, P, b, p, out, ldq);
+    else
+        get_basis_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(Q), n, m, P, b, p,
+                                                          out, ldq);
     return cudaGetLastError();
 }
 
