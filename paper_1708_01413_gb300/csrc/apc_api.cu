@@ -169,6 +169,13 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         a.gamma = gamma;
         a.eta = eta;
         a.inv_m = 1.0 / c->m;
+        auto split = [](double v, float &hi, float &lo) {
+            hi = float(v);
+            lo = float(v - double(hi));
+        };
+        split(gamma, a.g_hi, a.g_lo);
+        split(eta / c->m, a.em_hi, a.em_lo);
+        split(1.0 - eta, a.e1_hi, a.e1_lo);
         a.timeout_ns = uint64_t(c->timeout_s * 1e9);
         CK(c, cudaMemsetAsync(c->bar, 0, sizeof(uint32_t), s));
         cudaError_t e = launch_iter(c->precision, c->cpl, a, c->clusters, c->smem, s);

@@ -34,6 +34,8 @@ struct IterArgs {
     int64_t t0;         // global pass counter at launch (z buffer rotation)
     int64_t iters;      // passes in this launch
     double gamma, eta, inv_m;
+    // FP32 splits (hi + lo) of gamma, eta/m and 1 - eta for the FP32 / BF16 path
+    float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo;
     uint64_t timeout_ns;
 };
 

@@ -280,10 +280,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     const bool rx = Row::reads_x(mode), wx = Row::writes_x(mode);
     const size_t mP = size_t(m) * P;
     const size_t qrow = size_t(m) * P;  // elements per row of Q
-    const float g_hi = float(a.gamma);
-    const float g_lo = float(a.gamma - double(g_hi));
-    const float2 c_em = df_from(a.eta * a.inv_m);  // eta / m
-    const float2 c_1e = df_from(1.0 - a.eta);      // 1 - eta
+    const float g_hi = a.g_hi, g_lo = a.g_lo;
+    const float2 c_em = make_float2(a.em_hi, a.em_lo);  // eta / m
+    const float2 c_1e = make_float2(a.e1_hi, a.e1_lo);  // 1 - eta
+
+    // byte offsets of this lane's Q vectors within a stage: [slot][row][vector]
+    uint32_t qoff[WPW][R][H];
+#pragma unroll
+    for (int sl = 0; sl < WPW; ++sl)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+                qoff[sl][r][h] = uint32_t((r * L.row_stride + (warp * WPW + sl) * P + (h * 32 + lane) * V) * sizeof(TQ));
+    const uint32_t stage_bytes = uint32_t(L.stage_elems * sizeof(TQ));
+    const unsigned char *stage_bytes_base = smem;
 
     // element warps: lane (r_l, s_l) updates row r_l of worker slot s_l
     const int r_l = lane >> 4, s_l = lane & 15;
@@ -302,6 +313,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         const double v = a.xbar[row0 + i];
         xbd[i] = v;
         xbf[i] = df_from(v);
+    }
+    // Zero the stage ring once: rows past the end of a group and worker slots
+    // past the CTA's last worker are never written by TMA, so the element loops
+    // below read finite values there and need no per-row or per-slot guards
+    // (their results are discarded or multiplied by zero).
+    {
+        uint4 *p = reinterpret_cast<uint4 *>(smem);
+        const size_t n16 = size_t(S) * L.stage_elems * sizeof(TQ) / 16;
+        for (size_t i = tid; i < n16; i += blockDim.x) p[i] = make_uint4(0, 0, 0, 0);
+        fence_proxy_async_shared();
     }
     __syncthreads();
     cluster_sync_all();  // peers' barriers are initialised before any st.async
@@ -375,22 +396,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                         abort_flag = 1;
                         abort_code = DEV_TIMEOUT_TMA;
                     }
-                    const TQ *st = stage_base + size_t(st1) * L.stage_elems;
+                    const unsigned char *stb = stage_bytes_base + uint32_t(st1) * stage_bytes;
                     TC dsum[WPW];
 #pragma unroll
                     for (int sl = 0; sl < WPW; ++sl) {
-                        const int wl = warp * WPW + sl;
                         TC dr[R];
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             TC d0 = TC(0), d1 = TC(0);
-                            if (wl < W_cta && r < nr) {
 #pragma unroll
-                                for (int h = 0; h < H; ++h) {
-                                    TC qv[V];
-                                    load_row<TQ, TC, V>(st + r * L.row_stride + wl * P + (h * 32 + lane) * V, qv);
-                                    dot_vec<TC, V>(d0, d1, qv, &z[sl][h * V]);
-                                }
+                            for (int h = 0; h < H; ++h) {
+                                TC qv[V];
+                                load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
+                                dot_vec<TC, V>(d0, d1, qv, &z[sl][h * V]);
                             }
                             dr[r] = d0 + d1;
                         }
@@ -466,7 +484,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
             if (!is_ctl) {
                 // ---- second product of group t-2: z_i' += Q_i[j,:]^T coef_i[j] ----
                 if (has2) {
-                    const TQ *st = stage_base + size_t(st2) * L.stage_elems;
+                    const unsigned char *stb = stage_bytes_base + uint32_t(st2) * stage_bytes;
                     TC myc = TC(0);
                     if (upd_active && r_l < nr2) {
                         if constexpr (kDF) {
@@ -478,17 +496,14 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                     }
 #pragma unroll
                     for (int sl = 0; sl < WPW; ++sl) {
-                        const int wl = warp * WPW + sl;
 #pragma unroll
                         for (int r = 0; r < R; ++r) {
                             const TC cr = __shfl_sync(0xffffffffu, myc, r * 16 + sl);
-                            if (wl < W_cta && r < nr2) {
 #pragma unroll
-                                for (int h = 0; h < H; ++h) {
-                                    TC qv[V];
-                                    load_row<TQ, TC, V>(st + r * L.row_stride + wl * P + (h * 32 + lane) * V, qv);
-                                    axpy_vec<TC, V>(&acc[sl][h * V], qv, cr);
-                                }
+                            for (int h = 0; h < H; ++h) {
+                                TC qv[V];
+                                load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
+                                axpy_vec<TC, V>(&acc[sl][h * V], qv, cr);
                             }
                         }
                     }

@@ -56,6 +56,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
+// Order this thread's earlier generic-proxy shared-memory writes before later
+// async-proxy (TMA) accesses of the same memory.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ---- TMA bulk copy global -> shared (1-D, 16-byte aligned, size % 16 == 0)
 __device__ __forceinline__ uint64_t policy_evict_first() {
     uint64_t p;
