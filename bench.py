@@ -1,24 +1,32 @@
 """Benchmark of the APC hot loop on one GB300.
 
-Workload: the precision configuration of the solver's headline metric:
-A = D_r G D_c (32768 x 32768, G i.i.d. N(0,1), D log-uniform in [1e-2, 1e2]),
-m = 128 contiguous row blocks of 256 rows, Q_i stored in BF16 (2 GiB), FP32
-accumulation, FP64 setup.  One step = `--iters-per-step` APC iterations of
-Eq. (cons) in one persistent launch; `value` is APC iterations per second with
-everything resident in HBM.  Q (2 GiB) is far larger than L2 (129 MB), so no
-flush is needed between steps.
+Workload (headline metric): A = D_r G D_c, 32768 x 32768, G i.i.d. N(0,1),
+D_r, D_c diagonal log-uniform in [1e-2, 1e2]; m = 128 contiguous row blocks of
+256 rows; Q_i stored in BF16 (2 GiB), FP32 accumulation, FP64 setup.  One step
+= `--iters-per-step` APC iterations of Eq. (cons) in one persistent launch.
+`value` = APC iterations per second with everything resident in HBM.  Q
+(2 GiB) is far larger than L2 (129 MB), so no flush is needed between steps.
 
-Also reported on the same line: the FP32 path on the same matrix, the setup
-time, `e2e` (the same metric through the C ABI with host buffers: H2D of the
-right-hand side, least-norm reset, the iterations, D2H of xbar), the roofline
-of the iteration kernel, and the FP64 CPU oracle timed on a bounded sample.
+Also on the same JSON line:
+  e2e          the same metric through the C ABI with host buffers: per step an
+               H2D copy of the right-hand side, the least-norm reset, the
+               iterations and a D2H copy of xbar;
+  roofline     of the iteration kernel (algorithmic bytes / launch time);
+  fp32         the FP32 path on the same matrix;
+  tts          time to relative residual 1e-10, BF16 + FP64 refinement against
+               FP32 + FP64 refinement (and the floor of plain FP32), on a tall
+               Gaussian system (2304 x 2048, 9 blocks of 256, kappa(X) ~ 1e3): the
+               32768 scaled matrix has kappa(X) ~ 1e12 and needs far more
+               iterations than a benchmark can run;
+  cpu_baseline the FP64 oracle timed on a bounded sample (8 of the 128 blocks).
 
-`--impl reference` times the FP64 CPU oracle alone (the paper has no code; the
-oracle is the reference implementation of the method).
+`--impl reference` times the FP64 CPU oracle alone on the same workload (the
+paper has no code; the oracle is the reference implementation of the method).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -32,37 +40,67 @@ sys.path.insert(0, ROOT)
 
 N_FULL, M_FULL = 32768, 128
 METRIC = "time to 1e-10 rel. residual & APC iter/s at n=32768: BF16+IR vs FP32, HBM %"
+KERNEL_SOURCES = ("apc_iter_impl.cuh", "apc_iter.cu", "apc_iter_bf16.cu", "apc_iter_f32.cu", "apc_iter_f64.cu",
+                  "apc_ptx.cuh", "apc_internal.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "apc_iter_kernel_traffic.md")
+SAMPLE_BLOCKS = 8
 
 
-def _peaks():
+def kernel_source_hash():
+    """Hash of the iteration kernel's sources: a DRAM traffic figure measured
+    with ncu is reported only while the kernel is unchanged."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1708_01413_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_key):
+    """DRAM bytes per iteration of the iteration kernel for `workload_key`, from
+    the committed ncu summary; None if absent or taken on other sources."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    src, val = None, None
+    for line in open(TRAFFIC_FILE):
+        line = line.strip().strip("`")
+        if line.startswith("source_hash:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith(f"traffic_bytes_per_iteration[{workload_key}]:"):
+            val = float(line.split(":", 1)[1].strip())
+    return val if src == kernel_source_hash() else None
+
+
+def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         try:
             d = json.load(open(path))
-            return float(d.get("hbm_gbs", 6800.0)), "measured"
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
         except Exception:
             pass
     return 6800.0, "fallback"
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
-        self.index = index
-        self.rows = []
-        self.proc = None
+        self.index, self.rows, self.proc = index, [], None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            threading.Thread(target=self._read, daemon=True).start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -80,47 +118,22 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        reasons = set()
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        rows = [r for r in self.rows if len(r) >= 9]
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
-            if len(r) >= 9:
-                for nm, v in zip(names, r[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(nm)
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def _dist():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    return world, rank
-
-
-def oracle_sample(A_rows_host, offs_sample, m_total, iters, warm=1):
-    """Time the FP64 oracle's iteration on a sample of the row blocks.
-
-    Returns seconds per full-workload iteration (sample time scaled by
-    m_total / m_sample) and the thread count numpy used."""
-    import numpy as np
-    from oracle import apc_oracle as O
-    m_s = len(offs_sample) - 1
-    b = np.zeros(A_rows_host.shape[0])
-    blocks = O.partition(A_rows_host, b, offs_sample)
-    Qs = [O.block_qr(Ai)[0] for Ai, _ in blocks]
-    n = A_rows_host.shape[1]
-    rng = np.random.default_rng(0)
-    xs = [rng.standard_normal(n) for _ in range(m_s)]
-    xbar = sum(xs) / m_s
-    for _ in range(warm):
-        xs, xbar = O.apc_step(xs, xbar, Qs, 1.0, 1.5)
-    t0 = time.perf_counter()
-    for _ in range(iters):
-        xs, xbar = O.apc_step(xs, xbar, Qs, 1.0, 1.5)
-    dt = (time.perf_counter() - t0) / iters
-    return dt * (m_total / m_s)
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
 
 
 def _threads():
@@ -130,23 +143,58 @@ def _threads():
     return os.cpu_count() or 1
 
 
+# ---------------------------------------------------------------------------
+# FP64 oracle on a bounded sample (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+class OracleSample:
+    """The FP64 oracle's iteration on SAMPLE_BLOCKS of the workload's row
+    blocks; one step's time is scaled by m_total / SAMPLE_BLOCKS."""
+
+    def __init__(self, A_rows, p, m_total):
+        import numpy as np
+        from oracle import apc_oracle as O
+        self.O = O
+        rows = A_rows.shape[0]
+        offs = np.arange(0, rows + 1, p)
+        blocks = O.partition(A_rows, np.zeros(rows), offs)
+        self.Qs = [O.block_qr(Ai)[0] for Ai, _ in blocks]
+        rng = np.random.default_rng(0)
+        n = A_rows.shape[1]
+        self.xs = [rng.standard_normal(n) for _ in self.Qs]
+        self.xbar = sum(self.xs) / len(self.xs)
+        self.scale = m_total / len(self.Qs)
+
+    def step_seconds(self):
+        t0 = time.perf_counter()
+        self.xs, self.xbar = self.O.apc_step(self.xs, self.xbar, self.Qs, 1.0, 1.5)
+        return (time.perf_counter() - t0) * self.scale
+
+    def describe(self, n, p, m):
+        return (f"{len(self.Qs)} of {m} row blocks ({len(self.Qs) * p} x {n} FP64) of the workload, one Eq. (cons) "
+                f"iteration per step, time scaled x{self.scale:g} to all blocks")
+
+
+def _sample_rows(n, p, seed):
+    """The first SAMPLE_BLOCKS row blocks of the scaled system (host draw)."""
+    import numpy as np
+    rows = SAMPLE_BLOCKS * p
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((rows, n))
+    d_r = 10.0 ** rng.uniform(-2, 2, size=rows)
+    d_c = 10.0 ** rng.uniform(-2, 2, size=n)
+    return (d_r[:, None] * G) * d_c[None, :]
+
+
 def run_reference(args):
     world, rank = _dist()
     if rank != 0:
         return
-    import numpy as np
-    from paper_1708_01413_gb300 import inputs
-    rows = 8 * 256
-    A, _, _ = inputs.scaled_system(256, 0)  # warm numpy
-    rng = np.random.default_rng(0)
-    G = rng.standard_normal((rows, N_FULL))
-    d_r = 10.0 ** rng.uniform(-2, 2, size=rows)
-    d_c = 10.0 ** rng.uniform(-2, 2, size=N_FULL)
-    A_s = (d_r[:, None] * G) * d_c[None, :]
-    offs = np.arange(0, rows + 1, 256)
+    p = args.n // args.m
+    sample = OracleSample(_sample_rows(args.n, p, 0), p, args.m)
     times = []
     for s in range(args.warmup + args.steps):
-        t = oracle_sample(A_s, offs, M_FULL, iters=1, warm=0)
+        t = sample.step_seconds()
         if s >= args.warmup:
             times.append(t)
     sec = statistics.mean(times)
@@ -155,13 +203,84 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "APC n=32768 D_r G D_c, m=128 blocks of 256, FP64 CPU oracle sample"},
+        "config": {"workload": f"APC n={args.n} A=D_r G D_c (log-uniform 1e-2..1e2), m={args.m} blocks of {p}"},
         "cpu_baseline": {"value": value, "unit": "iter/s", "cores": _threads(), "kind": "oracle",
-                         "sample": "8 of 128 row blocks (2048 x 32768 FP64), one Eq. (cons) iteration per step, "
-                                   "time scaled x16 to all blocks"},
+                         "sample": sample.describe(args.n, p, args.m)},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def _ev():
+    import torch
+    return torch.cuda.Event(enable_timing=True)
+
+
+def time_to_tolerance(dev, tol=1e-10):
+    """Time to relative residual `tol`: BF16 + FP64 refinement against FP32 +
+    FP64 refinement (and the floor of plain FP32), on a tall Gaussian system
+    (N = 2304 equations, n = 2048 unknowns, 9 blocks of 256; kappa(X) ~ 1e3).
+    (gamma*, eta*) from Theorem 1 with the extreme eigenvalues of
+    X = (1/m) sum_i Q_i Q_i^T, from a host eigensolve of the GPU's FP64 bases."""
+    import numpy as np
+    import torch
+    from paper_1708_01413_gb300 import apc, inputs
+    n, N, m = 2048, 2304, 9
+    A, x_true, b = inputs.gaussian_system(n, 11, N=N)
+    offs = inputs.even_offsets(N, m)
+    At, bt = torch.tensor(A, device=dev), torch.tensor(b, device=dev)
+    ctx64 = apc.apc_setup(At, bt, offs, precision="f64")
+    X = sum(q @ q.T for q in (ctx64.basis(i).cpu().numpy() for i in range(m))) / m
+    ctx64.close()
+    mu = np.linalg.eigvalsh(X)
+    g, e, rho = apc.apc_optimal_params(float(mu[0]), float(mu[-1]))
+    out = {"workload": f"tall Gaussian N={N}, n={n}, m={m} blocks of {N // m}", "kappa_X": float(mu[-1] / mu[0]),
+           "gamma": g, "eta": e, "rho": rho, "tol": tol}
+    runs = (("bf16_ir", "bf16", True), ("f32_ir", "f32", True), ("f32_plain", "f32", False))
+    for key, prec, refine in runs:
+        ctx = apc.apc_setup(At, bt, offs, precision=prec)
+        ctx.solve(g, e, tol=tol, max_iters=200, check_every=50, refine=refine, raise_on_error=False)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, st = ctx.solve(g, e, tol=tol, max_iters=20000, check_every=50, refine=refine, raise_on_error=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xh = x.cpu().numpy()
+        out[key] = {"seconds": dt, "iterations": st["iterations"], "sweeps": st["sweeps"],
+                    "rel_residual": st["rel_residual"],
+                    "rel_error": float(np.linalg.norm(xh - x_true) / np.linalg.norm(x_true)),
+                    "converged": st["rc"] == 0}
+        ctx.close()
+    return out
+
+
+def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
+    """The FP32 path (Q in FP32) on the same matrix: iterations/s and HBM GB/s."""
+    import torch
+    from paper_1708_01413_gb300 import apc
+    n, m = A.shape[1], len(offs) - 1
+    c32 = apc.apc_setup(A, b, offs, precision="f32")
+    try:
+        c32.reset()
+        c32.iterate(gamma, eta, T)
+        torch.cuda.synchronize()
+        a0, a1 = _ev(), _ev()
+        a0.record(stream)
+        for _ in range(3):
+            c32.iterate(gamma, eta, T)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        s32 = a0.elapsed_time(a1) / 1e3
+        b32 = c32.info()["q_bytes"] + 2 * m * n * 4 + 2 * n * 8
+        gbs = b32 * 3 * T / s32 / 1e9
+        return {"iter_per_s": 3 * T / s32, "hbm_gbs": gbs, "frac": gbs / peak,
+                "cluster_size": c32.info()["cluster_size"]}
+    finally:
+        c32.close()
 
 
 def run_ours(args):
@@ -172,11 +291,11 @@ def run_ours(args):
     world, rank = _dist()
     if world > 1:
         import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-        local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
     dev = torch.device("cuda", torch.cuda.current_device())
     n, m = args.n, args.m
+    p = n // m
     A, x_true, b = inputs.scaled_system_torch(n, 1234 + rank, dev)
     offs = inputs.even_offsets(n, m)
     torch.cuda.synchronize()
@@ -185,20 +304,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     info = ctx.info()
-    gamma, eta = 1.0, 1.5  # any (gamma, eta) in S; the throughput does not depend on them
-    ctx.reset()
+    gamma, eta = 1.0, 1.5  # any (gamma, eta) in S: the time per iteration does not depend on them
     T = args.iters_per_step
     stream = torch.cuda.current_stream()
+    ctx.reset()
     for _ in range(args.warmup):
         ctx.iterate(gamma, eta, T)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(_ev(), _ev()) for _ in range(args.steps)]
     with ClockSampler(torch.cuda.current_device()) as clk:
         torch.cuda.synchronize()
-        t_start = torch.cuda.Event(enable_timing=True)
-        t_end = torch.cuda.Event(enable_timing=True)
+        t_start, t_end = _ev(), _ev()
         t_start.record(stream)
         for s in range(args.steps):
             ev[s][0].record(stream)
@@ -209,82 +327,81 @@ def run_ours(args):
     total_ms = t_start.elapsed_time(t_end)
     if world > 1:
         tt = torch.tensor([total_ms], device=dev)
+        torch.distributed.barrier()
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(tt.item())
-    launch_ms = [a.elapsed_time(bb) for a, bb in ev]
-    iters = args.steps * T
-    value = iters * world / (total_ms / 1e3)
-    ms_per_step = total_ms / args.steps
+    value = args.steps * T * world / (total_ms / 1e3)
 
-    # roofline of the iteration kernel: algorithmic bytes per launch / launch time
+    # roofline of the iteration kernel: algorithmic bytes per launch / launch time.
+    # Per iteration: Q once, x_i read + written (FP32 or FP64), xbar read + written.
     q_bytes = info["q_bytes"]
-    state_bytes = 2 * m * n * 4 + 2 * n * 8  # x_i read + write, xbar read + write
-    bytes_per_iter = q_bytes + state_bytes
-    avg_launch_s = statistics.mean(launch_ms) / 1e3
-    achieved = bytes_per_iter * T / avg_launch_s / 1e9
-    peak, peak_kind = _peaks()
+    s_bytes = 8 if args.precision == "f64" else 4
+    bytes_per_iter = q_bytes + 2 * m * n * s_bytes + 2 * n * 8
+    launch_s = statistics.mean(a.elapsed_time(bb) for a, bb in ev) / 1e3
+    achieved = bytes_per_iter * T / launch_s / 1e9
+    peak, peak_kind = hbm_peak()
+    tpi = measured_traffic(f"n={n},m={m},{args.precision}")
 
-    # e2e through the C ABI with host buffers: H2D rhs, reset, T iterations, D2H xbar
-    b_host = b.cpu().pin_memory()
-    x_host = torch.empty(n, dtype=torch.float64).pin_memory()
-    b_dev = torch.empty_like(b)
-    x_dev = torch.empty(n, dtype=torch.float64, device=dev)
-    e2e_steps = max(2, min(args.steps, 5))
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        b_dev.copy_(b_host, non_blocking=True)
-        ctx.reset(b_dev)
-        ctx.iterate(gamma, eta, T)
-        ctx.xbar(out=x_dev)
-        x_host.copy_(x_dev, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_value = e2e_steps * T / (e0.elapsed_time(e1) / 1e3)
+    e2e = None
+    if args.e2e:
+        b_host = b.cpu().pin_memory()
+        x_host = torch.empty(n, dtype=torch.float64).pin_memory()
+        b_dev = torch.empty_like(b)
+        x_dev = torch.empty(n, dtype=torch.float64, device=dev)
+        k = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0, e1 = _ev(), _ev()
+        e0.record(stream)
+        for _ in range(k):
+            b_dev.copy_(b_host, non_blocking=True)
+            ctx.reset(b_dev)
+            ctx.iterate(gamma, eta, T)
+            ctx.xbar(out=x_dev)
+            x_host.copy_(x_dev, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": k * T / (e0.elapsed_time(e1) / 1e3), "unit": "iter/s", "h2d_bytes_per_step": n * 8,
+               "d2h_bytes_per_step": n * 8}
 
     extra = {}
-    if args.fp32 and rank == 0:
-        ctx32 = apc.apc_setup(A, b, offs, precision="f32", cluster_size=0)
-        ctx32.reset()
-        ctx32.iterate(gamma, eta, 20)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        ctx32.iterate(gamma, eta, T)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        s32 = a0.elapsed_time(a1) / 1e3
-        b32 = ctx32.info()["q_bytes"] + state_bytes
-        extra["fp32"] = {"iter_per_s": T / s32, "hbm_gbs": b32 * T / s32 / 1e9, "q_bytes": ctx32.info()["q_bytes"]}
-        ctx32.close()
+    if args.fp32 and rank == 0 and args.precision != "f32":
+        ctx.close()
+        try:
+            extra["fp32"] = time_fp32(A, b, offs, gamma, eta, T, peak, stream)
+        except Exception as exc:  # a failed comparison must not lose the headline number
+            extra["fp32"] = {"error": str(exc)}
+    if args.tts and rank == 0:
+        try:
+            extra["tts"] = time_to_tolerance(dev)
+        except Exception as exc:
+            extra["tts"] = {"error": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rows = 8 * 256
-        A_s = A[:rows].cpu().numpy()
-        sec = oracle_sample(A_s, np.arange(0, rows + 1, 256), m, iters=2)
+        A_s = A[:SAMPLE_BLOCKS * p].cpu().numpy()
+        del A
+        sample = OracleSample(A_s, p, m)
+        secs = [sample.step_seconds() for _ in range(3)]
+        sec = statistics.mean(secs[1:])
         cpu = {"value": 1.0 / sec, "unit": "iter/s", "cores": _threads(), "kind": "oracle",
-               "sample": "8 of 128 row blocks (2048 x 32768 FP64) of the same matrix, 2 Eq. (cons) "
-                         "iterations, time scaled x16 to all blocks"}
+               "sample": sample.describe(n, p, m)}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": f"APC n={n} A=D_r G D_c (log-uniform 1e-2..1e2), m={m} blocks of {n // m}, "
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"APC n={n} A=D_r G D_c (log-uniform 1e-2..1e2), m={m} blocks of {p}, "
                                    f"Q {args.precision}, FP32 accumulation",
                        "iters_per_step": T, "l2": f"Q {q_bytes / 2**30:.2f} GiB > L2 129 MB, no flush",
                        "cluster_size": info["cluster_size"], "clusters": info["clusters"],
-                       "setup_s": setup_s},
-            "e2e": {"value": e2e_value, "unit": "iter/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
-            "gpu_launches": args.steps * (1 + (T > (1 << 20))),
+                       "setup_s": round(setup_s, 3)},
+            "e2e": e2e,
+            "gpu_launches": args.steps * ((T + (1 << 20) - 1) >> 20),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "kernel": "apc_iter_kernel", "bytes_per_iter": bytes_per_iter},
+                         "frac": achieved / peak, "traffic": (tpi * T if tpi is not None else None),
+                         "peak_kind": peak_kind, "kernel": "apc_iter_kernel (MODE_APC)",
+                         "algorithmic_bytes_per_launch": bytes_per_iter * T, "source_hash": kernel_source_hash()},
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
@@ -305,7 +422,9 @@ def main():
     p.add_argument("--precision", default="bf16", choices=["bf16", "f32", "f64"])
     p.add_argument("--iters-per-step", type=int, default=100)
     p.add_argument("--cluster-size", type=int, default=0)
-    p.add_argument("--fp32", type=int, default=1)
+    p.add_argument("--fp32", type=int, default=1, help="also time the FP32 path on the same matrix")
+    p.add_argument("--tts", type=int, default=1, help="also measure time to 1e-10 (BF16+IR vs FP32+IR)")
+    p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
     if args.impl == "reference":

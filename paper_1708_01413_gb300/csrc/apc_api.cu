@@ -92,10 +92,9 @@ int configure(apc_ctx *c, int cs_request, int wpw_request) {
     CK(c, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     const int R = kRowsPerGroup;
     const size_t qsz = q_elem_size(c->precision);
-    const size_t budget = size_t(smem_optin) - 4 * 1024;
+    const size_t budget = size_t(smem_optin) - 2 * 1024;
     const int cands[4] = {1, 2, 4, 8};
-    int best = -1, best_wpw = 0, best_nw = 0, best_stages = 0;
-    for (int ci = 0; ci < 4 && best < 0; ++ci) {
+    for (int ci = 0; ci < 4; ++ci) {
         const int cs = cands[ci];
         if (cs_request > 0 && cs != cs_request) continue;
         const int W0 = (c->m + cs - 1) / cs;
@@ -105,43 +104,35 @@ int configure(apc_ctx *c, int cs_request, int wpw_request) {
         const int W = nw * wpw;  // worker slots per CTA
         if (W > 32 || nw > kMaxElemWarps || (cs - 1) * W >= c->m) continue;
         const size_t stage = size_t(R) * W * c->P * qsz;
-        const int64_t rpc_guess = (c->n + std::max(1, dev_sms / cs) - 1) / std::max(1, dev_sms / cs);
-        const size_t fixed = iter_smem_bytes(c->precision, c->P, W, 0, rpc_guess) + 1024;
-        if (fixed >= budget) continue;
-        const int stages = int(std::min<size_t>(6, (budget - fixed) / stage));
-        const int min_stages = kMinStages;
-        if (stages < min_stages) continue;
-        best = cs;
-        best_wpw = wpw;
-        best_nw = nw;
-        best_stages = stages;
-    }
-    if (best < 0)
-        return fail(c, APC_ERR_UNSUPPORTED, "no cluster size fits m=%d blocks of width %d (requested cs=%d wpw=%d)",
-                    c->m, c->P, cs_request, wpw_request);
-    c->cs = best;
-    c->wpw = best_wpw;
-    c->nw = best_nw;
-    c->stages = best_stages;
-    const int W = c->nw * c->wpw;
-    int64_t clusters = std::max(1, dev_sms / best);
-    clusters = std::min<int64_t>(clusters, (c->n + R - 1) / R);
-    for (int pass = 0; pass < 3; ++pass) {
+        // clusters that fit with the smallest ring, then the deepest ring that fits
+        int64_t clusters = std::min<int64_t>(std::max(1, dev_sms / cs), (c->n + R - 1) / R);
+        int stages = 0;
+        size_t smem = 0;
+        bool ok = false;
+        for (int pass = 0; pass < 4 && !ok; ++pass) {
+            const int64_t rpc = (c->n + clusters - 1) / clusters;
+            const size_t fixed = iter_smem_bytes(c->precision, c->P, W, 0, rpc);
+            if (fixed + size_t(kMinStages) * stage > budget) break;
+            stages = int(std::min<size_t>(6, (budget - fixed) / stage));
+            smem = iter_smem_bytes(c->precision, c->P, W, stages, rpc);
+            const int maxc = iter_max_clusters(c->precision, c->cpl, wpw, cs, nw, smem);
+            if (maxc <= 0) break;
+            if (maxc >= clusters) ok = true;
+            else clusters = maxc;
+        }
+        if (!ok) continue;
+        c->cs = cs;
+        c->wpw = wpw;
+        c->nw = nw;
+        c->stages = stages;
+        c->clusters = int(clusters);
         c->rows_per_cluster = (c->n + clusters - 1) / clusters;
-        c->smem = iter_smem_bytes(c->precision, c->P, W, c->stages, c->rows_per_cluster);
-        if (c->smem > budget)
-            return fail(c, APC_ERR_UNSUPPORTED, "shared memory %zu exceeds %zu", c->smem, budget);
-        const int maxc = iter_max_clusters(c->precision, c->cpl, c->wpw, best, c->nw, c->smem);
-        if (maxc <= 0)
-            return fail(c, APC_ERR_LAUNCH, "no co-resident cluster of %d CTAs x %d threads with %zu B shared memory",
-                        best, c->nw * 32, c->smem);
-        if (maxc >= clusters) break;
-        clusters = maxc;
+        c->smem = smem;
+        return APC_OK;
     }
-    c->clusters = int(clusters);
-    c->rows_per_cluster = (c->n + clusters - 1) / clusters;
-    c->smem = iter_smem_bytes(c->precision, c->P, W, c->stages, c->rows_per_cluster);
-    return APC_OK;
+    return fail(c, APC_ERR_UNSUPPORTED,
+                "no launch configuration fits m=%d blocks of width %d, n=%lld (requested cs=%d wpw=%d)", c->m, c->P,
+                (long long)c->n, cs_request, wpw_request);
 }
 
 int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {

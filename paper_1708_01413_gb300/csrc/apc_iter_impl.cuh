@@ -60,9 +60,11 @@ struct SmemLayout {
     __host__ __device__ SmemLayout(size_t q_elem, size_t s_elem, int slots, int P, int stages, int64_t rpc) {
         row_stride = size_t(slots) * P;               // elements per staged row
         stage_elems = size_t(R) * row_stride;
-        off_xbd = align_up(size_t(stages) * stage_elems * q_elem, 128);  // xbar, FP64 [2][rpc]
-        off_xbf = align_up(off_xbd + 2 * size_t(rpc) * 8, 16);         // xbar, FP32 hi/lo [2][rpc]
-        off_red = align_up(off_xbf + 2 * size_t(rpc) * 8, 16);         // per-slot row terms [2][R][32]
+        // xbar [2][rpc], 8 bytes per row: FP64, or an FP32 hi/lo pair on the
+        // double-float path (one launch uses one of the two views)
+        off_xbd = align_up(size_t(stages) * stage_elems * q_elem, 128);
+        off_xbf = off_xbd;
+        off_red = align_up(off_xbd + 2 * size_t(rpc) * 8, 16);         // per-slot row terms [2][R][32]
         off_sloc = align_up(off_red + 2 * R * 32 * s_elem, 16);        // cluster row sums [NX][8][R]
         off_xbn = off_sloc + size_t(NX) * 8 * R * 8;                   // new xbar of a group [2][R] (hi/lo)
         off_bars = align_up(off_xbn + 2 * R * 8, 8);
@@ -311,8 +313,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     }
     for (int i = tid; i < nrows; i += blockDim.x) {
         const double v = a.xbar[row0 + i];
-        xbd[i] = v;
-        xbf[i] = df_from(v);
+        if constexpr (kDF) xbf[i] = df_from(v);
+        else xbd[i] = v;
     }
     // Zero the stage ring once: rows past the end of a group and worker slots
     // past the CTA's last worker are never written by TMA, so the element loops
