@@ -126,6 +126,27 @@ int apc_get_basis(apc_ctx *ctx, int32_t block, double *Q_dev, int64_t ldq, void 
 int apc_residual(apc_ctx *ctx, const double *x_dev, const double *rhs_dev,
                  double *resid_dev, double *rel_residual_host, void *stream);
 
+/* apc_residual_noalloc -- the FP64 relative residual ||rhs - A x||_2 / ||rhs||_2
+ * (and, if resid_dev is not NULL, the vector rhs - A x), computed without
+ * allocating any device memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate at the moment they need the
+ * check (a framework that has reserved all device memory for its own pool, or
+ * a latency-critical path where cudaMalloc's implicit synchronisation is not
+ * acceptable).  It takes no context: the caller passes every input and output.
+ *   A_dev: N x n FP64 row-major, leading dimension lda >= n (device);
+ *   x_dev: n FP64; rhs_dev: N FP64; resid_dev: N FP64 or NULL (device);
+ *   rel_residual_host: result (host).  Synchronises `stream`.
+ * Working memory is a fixed array inside the library (about 512 KiB, held on
+ * every GPU that loads the library until the process exits), which limits
+ * N to 1,048,576 rows: larger N returns APC_ERR_UNSUPPORTED.  All calls share
+ * that array, so calls that overlap on the GPU (different streams or host
+ * threads on one device) race and may return wrong results.  The first call
+ * on a device looks up the array's address with that device current; make it
+ * before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, CUDA (text in
+ * apc_last_error(NULL)). */
+int apc_residual_noalloc(const double *A_dev, int64_t lda, int64_t N, int64_t n, const double *x_dev,
+                         const double *rhs_dev, double *resid_dev, double *rel_residual_host, void *stream);
+
 /* apc_solve -- run Algorithm 1 from the least-norm initialisation until the
  * FP64 relative residual ||b - A xbar|| / ||b|| <= tol, checking every
  * `check_every` iterations, or max_iters iterations.  With refine != 0 the

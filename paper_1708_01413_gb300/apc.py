@@ -70,6 +70,8 @@ def lib() -> C.CDLL:
     L.apc_solve.argtypes = [vp, dbl, dbl, dbl, i64, i64, i32, vp, C.POINTER(apc_stats), vp]
     L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                    C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+    L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
+    L.apc_residual_noalloc.restype = C.c_int
     L.apc_last_error.argtypes = [vp]
     L.apc_last_error.restype = C.c_char_p
     L.apc_destroy.argtypes = [vp]
@@ -179,6 +181,22 @@ class Context:
         if rc != 0 and raise_on_error:
             _check(rc, self.handle)
         return out, stats
+
+
+def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:
+    """||rhs - A x|| / ||rhs|| in FP64 without any device allocation (see the
+    header): A is an N x n row-major FP64 CUDA tensor, x and rhs FP64 CUDA
+    vectors, resid_out an optional N-vector receiving rhs - A x."""
+    import torch
+    for t in (A, x, rhs) + ((resid_out,) if resid_out is not None else ()):
+        if not t.is_cuda or t.dtype != torch.float64:
+            raise TypeError("float64 CUDA tensors expected")
+    if A.dim() != 2 or A.stride(1) != 1 or not x.is_contiguous() or not rhs.is_contiguous():
+        raise ValueError("A must be row-major; x and rhs contiguous")
+    rel = C.c_double()
+    _check(lib().apc_residual_noalloc(_ptr(A), A.stride(0), A.shape[0], A.shape[1], _ptr(x), _ptr(rhs),
+                                      _ptr(resid_out), C.byref(rel), _stream(stream)))
+    return rel.value
 
 
 def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,

@@ -198,6 +198,11 @@ int residual(apc_ctx *c, const double *x, const double *rhs, double *out, double
 
 }  // namespace
 
+namespace apc {
+// Error text for entry points that have no context (read by apc_last_error(NULL)).
+void set_global_error_text(const char *msg) { g_setup_error = msg; }
+}  // namespace apc
+
 extern "C" {
 
 int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho) {
