@@ -159,6 +159,30 @@ int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_it
               int64_t check_every, int32_t refine, double *x_dev, apc_stats *stats,
               void *stream);
 
+/* apc_backward -- reverse-mode sweep through T unrolled iterations.
+ * The forward map is b -> xbar(T): least-norm x_i(0), xbar(0) = mean, then T
+ * applications of Eq. (cons) with (gamma, eta) (apc_reset + apc_iterate).  It
+ * is linear in b, so its transpose needs no forward state.  Given
+ * g_dev = dL/dxbar(T) (FP64, n, device) this computes db_dev = dL/db (FP64, N,
+ * device) by the transposed step (P_i is symmetric, Sec. 3.1): with
+ * mu_i = lambda_i + (eta/m) lbar,
+ *   lambda_i <- (1 - gamma) mu_i + gamma Q_i Q_i^T mu_i,
+ *   lbar     <- (1 - eta) lbar + gamma sum_i (mu_i - Q_i Q_i^T mu_i),
+ * from lambda_i = 0, lbar = g, then db_i = (A_i^+)^T (lambda_i + lbar/m).
+ * Uses the context's iteration state (a later apc_iterate needs apc_reset).
+ * Errors: PARAMS (gamma outside (0, 2)), INVALID_ARG, TIMEOUT, CUDA. */
+int apc_backward(apc_ctx *ctx, const double *g_dev, int64_t T, double gamma, double eta, double *db_dev,
+                 void *stream);
+
+/* apc_set_test_hooks -- failure injection for tests, on the host side of a
+ * device wait: every grid barrier of later launches waits for
+ * grid_barrier_skew arrivals more than the grid has (0 = normal), and every
+ * device-side wait gives up after timeout_s seconds.  With a positive skew a
+ * launch of two or more iterations runs out of time at its first barrier,
+ * returns cleanly and apc_iterate reports APC_ERR_TIMEOUT; the context stays
+ * usable (apc_reset, then iterate).  Errors: INVALID_ARG. */
+int apc_set_test_hooks(apc_ctx *ctx, int32_t grid_barrier_skew, double timeout_s);
+
 /* apc_context_info -- sizes chosen at setup: padded block width, cluster
  * size, number of clusters and bytes of Q.  Any pointer may be NULL. */
 int apc_context_info(const apc_ctx *ctx, int64_t *n, int64_t *N, int32_t *m, int32_t *width,

@@ -25,7 +25,7 @@ ERRORS = {
 # Every function the header declares; tests check the library exports them.
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
-    "apc_get_basis", "apc_residual", "apc_solve", "apc_context_info", "apc_last_error", "apc_destroy",
+    "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
 )
 
 
@@ -70,6 +70,8 @@ def lib() -> C.CDLL:
     L.apc_solve.argtypes = [vp, dbl, dbl, dbl, i64, i64, i32, vp, C.POINTER(apc_stats), vp]
     L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                    C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+    L.apc_backward.argtypes = [vp, vp, i64, dbl, dbl, vp, vp]
+    L.apc_set_test_hooks.argtypes = [vp, i32, dbl]
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_residual_noalloc.restype = C.c_int
     L.apc_last_error.argtypes = [vp]
@@ -168,6 +170,20 @@ class Context:
                                   _stream(stream)), self.handle)
         return rel.value
 
+    def set_test_hooks(self, grid_barrier_skew: int = 0, timeout_s: float = 2.0):
+        """Failure injection for tests (see apc_set_test_hooks in the header)."""
+        _check(lib().apc_set_test_hooks(self.handle, int(grid_barrier_skew), float(timeout_s)), self.handle)
+
+    def backward(self, g, T: int, gamma: float, eta: float, out=None, stream=None):
+        """dL/db for L depending on xbar(T) through T iterations from the
+        least-norm initialisation; g = dL/dxbar(T) (FP64, n)."""
+        import torch
+        N = self.info()["N"]
+        out = torch.empty(N, dtype=torch.float64, device=self.device) if out is None else out
+        _check(lib().apc_backward(self.handle, _ptr(g.contiguous()), int(T), gamma, eta, _ptr(out),
+                                  _stream(stream)), self.handle)
+        return out
+
     def solve(self, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False,
               out=None, stream=None, raise_on_error=True):
         import torch
@@ -181,6 +197,45 @@ class Context:
         if rc != 0 and raise_on_error:
             _check(rc, self.handle)
         return out, stats
+
+
+class APCSolveFn:
+    """Differentiable T-iteration APC solve, xbar(T) = F(b), for torch.autograd.
+
+    ``APCSolveFn.apply(b, ctx, gamma, eta, T)``: b is an FP64 CUDA tensor of
+    shape (N,) or (N, k) (k right-hand sides, solved one after another); the
+    backward pass returns dL/db through ``Context.backward``."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, b, ctx, gamma, eta, T):
+        if cls._fn is None:
+            import torch
+
+            class _F(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, b, solver, gamma, eta, T):
+                    cols = b.unsqueeze(1) if b.dim() == 1 else b
+                    outs = []
+                    for j in range(cols.shape[1]):
+                        solver.reset(cols[:, j].contiguous())
+                        solver.iterate(gamma, eta, T)
+                        outs.append(solver.xbar())
+                    fctx.solver, fctx.gamma, fctx.eta, fctx.T, fctx.vec = solver, gamma, eta, T, b.dim() == 1
+                    x = torch.stack(outs, dim=1)
+                    return x[:, 0] if b.dim() == 1 else x
+
+                @staticmethod
+                def backward(fctx, gx):
+                    gcols = gx.unsqueeze(1) if fctx.vec else gx
+                    dbs = [fctx.solver.backward(gcols[:, j].contiguous(), fctx.T, fctx.gamma, fctx.eta)
+                           for j in range(gcols.shape[1])]
+                    db = torch.stack(dbs, dim=1)
+                    return (db[:, 0] if fctx.vec else db), None, None, None, None
+
+            cls._fn = _F
+        return cls._fn.apply(b, ctx, gamma, eta, T)
 
 
 def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:

@@ -35,6 +35,7 @@ struct apc_ctx {
     size_t smem = 0;
     int64_t t = 0;   // global pass counter (z buffer rotation)
     double timeout_s = 2.0;
+    uint32_t test_barrier_skew = 0;
     size_t q_bytes = 0;
     std::string last_error;
 };
@@ -168,6 +169,7 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         split(eta / c->m, a.em_hi, a.em_lo);
         split(1.0 - eta, a.e1_hi, a.e1_lo);
         a.timeout_ns = uint64_t(c->timeout_s * 1e9);
+        a.barrier_skew = c->test_barrier_skew;
         CK(c, cudaMemsetAsync(c->bar, 0, sizeof(uint32_t), s));
         cudaError_t e = launch_iter(c->precision, c->cpl, a, c->clusters, c->smem, s);
         if (e != cudaSuccess) return fail(c, APC_ERR_LAUNCH, "iteration kernel launch failed: %s", cudaGetErrorString(e));
@@ -509,6 +511,38 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     }
     return rc;
+}
+
+int apc_backward(apc_ctx *c, const double *g_dev, int64_t T, double gamma, double eta, double *db_dev,
+                 void *stream) {
+    if (!c || !g_dev || !db_dev || T < 0) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
+    if (!(gamma > 0.0 && gamma < 2.0) || !std::isfinite(eta))
+        return fail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2) and eta must be finite", gamma);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ssz = s_elem_size(c->precision);
+    // lambda_i = 0, lbar = g, z buffers cleared
+    CK(c, cudaMemsetAsync(c->xw, 0, ssz * c->n * c->m, s));
+    CK(c, cudaMemsetAsync(c->zbuf, 0, ssz * 3 * c->m * c->P, s));
+    CK(c, cudaMemcpyAsync(c->xbar, g_dev, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+    c->t = 0;
+    int rc;
+    // z = Q_i^T mu_i(T) with mu_i(T) = (eta/m) g
+    if ((rc = run_pass(c, MODE_ADJ_SEED, gamma, eta, 1, s)) != APC_OK) return rc;
+    if ((rc = run_pass(c, MODE_ADJ, gamma, eta, T, s)) != APC_OK) return rc;
+    // v_i = Q_i^T (lambda_i(0) + lbar(0)/m)
+    if ((rc = run_pass(c, MODE_ADJ_FINAL, gamma, eta, 1, s)) != APC_OK) return rc;
+    const void *v = static_cast<const char *>(c->zbuf) + ssz * size_t(c->t % 3) * c->m * c->P;
+    CK(c, launch_bsolve(v, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P, state_prec(c->precision),
+                        db_dev, s));
+    c->t = 0;  // the iteration state now holds the reverse sweep: apc_iterate needs apc_reset
+    return APC_OK;
+}
+
+int apc_set_test_hooks(apc_ctx *c, int32_t grid_barrier_skew, double timeout_s) {
+    if (!c || grid_barrier_skew < 0 || !(timeout_s > 0.0)) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
+    c->test_barrier_skew = uint32_t(grid_barrier_skew);
+    c->timeout_s = timeout_s;
+    return APC_OK;
 }
 
 int apc_context_info(const apc_ctx *c, int64_t *n, int64_t *N, int32_t *m, int32_t *width, int32_t *cluster_size,

@@ -37,6 +37,7 @@ struct IterArgs {
     // FP32 splits (hi + lo) of gamma, eta/m and 1 - eta for the FP32 / BF16 path
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo;
     uint64_t timeout_ns;
+    uint32_t barrier_skew;  // test hook: extra arrivals the grid barrier waits for (0 in use)
 };
 
 // Device error word values.

@@ -582,7 +582,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 if (tid == 0) {
                     __threadfence();
                     red_release_add_u32(a.bar, 1u);
-                    const uint32_t target = uint32_t(it + 1) * gridDim.x;
+                    const uint32_t target = uint32_t(it + 1) * gridDim.x + a.barrier_skew;
                     if (ld_acquire_u32(a.bar) < target) {
                         const uint64_t t_start = globaltimer_ns();
                         while (ld_acquire_u32(a.bar) < target) {

@@ -209,3 +209,89 @@ def test_basis_spans_row_space_and_projector_matches(prec, tol):
         P = np.eye(150) - Q @ Q.T
         assert np.abs(P - O.projector(Ai)).max() <= 4 * tol
         assert np.abs(Ai @ P).max() <= 4 * tol * np.abs(Ai).max() * np.sqrt(150)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-4)])
+def test_backward_matches_oracle_adjoint(prec, tol):
+    # dL/db through T unrolled iterations (transpose of Eq. (cons)) against the FP64 oracle sweep
+    apc, dev = _apc(), _dev()
+    n, m, T = 600, 6, 40
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 12)
+    xt = inputs.target_vector(n, 12)
+    xbar, _, _ = O.apc_forward_linear(blocks, Qs, Rs, g, e, T)
+    gT = xbar - xt
+    ref = np.concatenate(O.apc_adjoint(blocks, Qs, Rs, g, e, T, gT)[0])
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    db = ctx.backward(torch.tensor(gT, device=dev), T, g, e).cpu().numpy()
+    assert _rel(db, ref) <= tol
+    # the reverse sweep leaves the context usable for a fresh forward solve
+    ctx.reset()
+    ctx.iterate(g, e, 5)
+
+
+def test_autograd_grad_b_matches_central_difference():
+    # L = 0.5 ||xbar_T - x_target||^2 is quadratic in b: central differences of the
+    # FP64 oracle forward are exact up to rounding (spec bar: 1e-4 relative)
+    apc, dev = _apc(), _dev()
+    n, m, T, k = 512, 8, 40, 3
+    A, _, B = inputs.gaussian_system(n, 13, k=k)
+    offs = inputs.even_offsets(n, m)
+    blocks = O.partition(A, B, offs)
+    QR = [O.block_qr(Ai) for Ai, _ in blocks]
+    Qs, Rs = [q for q, _ in QR], [r for _, r in QR]
+    lo, hi = O.mu_bounds(Qs)
+    g, e, _ = O.optimal_params(lo, hi)
+    xt = inputs.target_vector(n, 13, k=k)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(B[:, 0].copy(), device=dev), offs, precision="f32")
+    bt = torch.tensor(B, device=dev, requires_grad=True)
+    x = apc.APCSolveFn.apply(bt, ctx, g, e, T)
+    loss = 0.5 * ((x - torch.tensor(xt, device=dev)) ** 2).sum()
+    loss.backward()
+    grad = bt.grad.cpu().numpy()
+
+    def L(Bv):
+        xb, _, _ = O.apc_forward_linear(O.partition(A, Bv, offs), Qs, Rs, g, e, T)
+        return 0.5 * float(np.sum((xb - xt) ** 2))
+
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        d = rng.standard_normal(B.shape)
+        h = 1e-2 * np.linalg.norm(B)
+        fd = (L(B + h * d) - L(B - h * d)) / (2 * h)
+        assert float(np.sum(grad * d)) == pytest.approx(fd, rel=1e-4)
+
+
+def test_backward_tends_to_inverse_transpose_at_convergence():
+    apc, dev = _apc(), _dev()
+    n, m = 200, 4
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 14)
+    tr = O.apc_run(A, b, offs, g, e, tol=1e-13, max_iters=200000, record_every=50, Qs=Qs, Rs=Rs)
+    gT = inputs.target_vector(n, 14)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64")
+    db = ctx.backward(torch.tensor(gT, device=dev), tr.iters, g, e).cpu().numpy()
+    ref = np.linalg.solve(A.T, gT)
+    assert _rel(db, ref) <= 1e-8
+
+
+def test_device_wait_timeout_is_reported_and_context_recovers():
+    # Failure detection without a GPU fault: the test hook makes every grid barrier
+    # wait for one CTA more than exists; the bounded wait runs out, the kernel
+    # returns, the host reports TIMEOUT, and the context still solves afterwards.
+    apc, dev = _apc(), _dev()
+    n, m, T = 400, 8, 20
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 15)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f32")
+    ctx.reset()
+    ctx.set_test_hooks(grid_barrier_skew=1, timeout_s=0.2)
+    import time
+    t0 = time.time()
+    with pytest.raises(apc.ApcError) as ei:
+        ctx.iterate(g, e, 3)
+    assert ei.value.name == "TIMEOUT"
+    assert "grid barrier" in str(ei.value)
+    assert time.time() - t0 < 10
+    ctx.set_test_hooks(grid_barrier_skew=0, timeout_s=2.0)
+    ctx.reset()
+    ctx.iterate(g, e, T)
+    ref = O.apc_run(A, b, offs, g, e, max_iters=T, Qs=Qs, Rs=Rs)
+    assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-5
