@@ -10,35 +10,11 @@
 #include <vector>
 
 #include "../../include/apc.h"
+#include "apc_ctx.h"
 #include "apc_internal.h"
 
 using namespace apc;
 
-struct apc_ctx {
-    int device = 0;
-    int precision = APC_F32;
-    int64_t N = 0, n = 0;
-    int m = 0, P = 0, cpl = 0;
-    std::vector<int64_t> offs;
-    int64_t *d_rowstart = nullptr;   // block b starts at row offs[b]
-    int32_t *d_p = nullptr;          // rows per block
-    double *A = nullptr, *b = nullptr, *dinv = nullptr;
-    double *Rinv1 = nullptr, *Rinv2 = nullptr;
-    void *Q = nullptr;
-    void *xw = nullptr, *zbuf = nullptr;
-    double *xbar = nullptr;  // master estimate, FP64 in every mode
-    uint32_t *bar = nullptr;
-    int *err = nullptr;
-    double *sums = nullptr, *xtmp = nullptr, *rtmp = nullptr, *xacc = nullptr, *rhs = nullptr;
-    int cs = 1, nw = 1, wpw = 1, stages = 2, clusters = 1;
-    int64_t rows_per_cluster = 1;
-    size_t smem = 0;
-    int64_t t = 0;   // global pass counter (z buffer rotation)
-    double timeout_s = 2.0;
-    uint32_t test_barrier_skew = 0;
-    size_t q_bytes = 0;
-    std::string last_error;
-};
 
 namespace {
 

@@ -49,8 +49,8 @@ cudaError_t launch_iter(int precision, int cpl, const IterArgs &a, int clusters,
                         cudaStream_t s);
 // Maximum number of co-resident clusters for a configuration (0 on failure).
 int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t smem);
-// Minimum ring depth: three stages are in use at a time.
-constexpr int kMinStages = 4;
+// Minimum ring depth: four stages are in use at a time.
+constexpr int kMinStages = 5;
 // Dynamic shared memory of one CTA: `slots` worker slots, `stages` ring stages.
 size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster);
 constexpr int kRowsPerGroup = 2;   // rows of Q per pipeline step

@@ -18,13 +18,15 @@
 // shared memory, completing on their mbarriers).  Partial z_i' of all clusters
 // are summed with global atomics, then one grid-wide barrier per iteration.
 //
-// Pipeline.  Rows go in groups of R = 2; one __syncthreads per step.  Step t
-// computes the first product and the machines' updates of group t and sends
-// the group's row sums to the cluster, and finishes group t-2: the master's
-// new xbar (FP64, one lane per row) and the second product.  The two steps in
-// between hide the cluster exchange.  Q rows stream into a ring of S
-// shared-memory stages through TMA bulk copies (L2 evict-first); three stages
-// are in use, S-3 are loading.
+// Pipeline.  Rows go in groups of R = 2; one __syncthreads per step.  Element
+// warps stream Q: step t computes the first product of group t and the second
+// product of group t-3.  Two control warps own one row of a group each, one
+// lane per worker slot: after the barrier of step t they finish the master's
+// update of group t-2 (its cluster exchange was sent two steps earlier) and
+// write the second product's coefficients, then apply the machines' updates
+// of group t, form the CTA row sum and send it to the cluster.  Q rows stream
+// into a ring of S shared-memory stages through TMA bulk copies (L2
+// evict-first); four stages are in use, S-4 are loading.
 //
 // Arithmetic (FP32 / BF16 Q).  Products accumulate in FP32 with packed FFMA2.
 // xbar is kept in FP64 and as an FP32 hi+lo pair.  The row sums travel as
@@ -42,6 +44,8 @@
 // records an error word, drains its own bulk copies, joins a final cluster
 // barrier and returns.
 #pragma once
+#include <type_traits>
+
 #include "apc_internal.h"
 #include "apc_ptx.cuh"
 
@@ -56,18 +60,17 @@ constexpr int DELAY = 2;           // steps between a group's first and second p
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemLayout {
-    size_t stage_elems, row_stride, off_xbd, off_xbf, off_red, off_sloc, off_xbn, off_bars, total;
+    size_t stage_elems, row_stride, off_xb, off_d, off_coef, off_sloc, off_bars, total;
     __host__ __device__ SmemLayout(size_t q_elem, size_t s_elem, int slots, int P, int stages, int64_t rpc) {
         row_stride = size_t(slots) * P;               // elements per staged row
         stage_elems = size_t(R) * row_stride;
         // xbar [2][rpc], 8 bytes per row: FP64, or an FP32 hi/lo pair on the
         // double-float path (one launch uses one of the two views)
-        off_xbd = align_up(size_t(stages) * stage_elems * q_elem, 128);
-        off_xbf = off_xbd;
-        off_red = align_up(off_xbd + 2 * size_t(rpc) * 8, 16);         // per-slot row terms [2][R][32]
-        off_sloc = align_up(off_red + 2 * R * 32 * s_elem, 16);        // cluster row sums [NX][8][R]
-        off_xbn = off_sloc + size_t(NX) * 8 * R * 8;                   // new xbar of a group [2][R] (hi/lo)
-        off_bars = align_up(off_xbn + 2 * R * 8, 8);
+        off_xb = align_up(size_t(stages) * stage_elems * q_elem, 128);
+        off_d = align_up(off_xb + 2 * size_t(rpc) * 8, 16);        // first-product results [2][R][32]
+        off_coef = align_up(off_d + 2 * R * 32 * s_elem, 16);      // second-product coefficients [2][32][R]
+        off_sloc = align_up(off_coef + 2 * 32 * R * s_elem, 16);   // cluster row sums [NX][8][R]
+        off_bars = align_up(off_sloc + size_t(NX) * 8 * R * 8, 8);
         total = off_bars + (stages + NX) * sizeof(uint64_t);
     }
 };
@@ -247,22 +250,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     __shared__ int abort_code;
 
     const int P = a.P, nwe = a.nw, S = a.stages, m = a.m, cs = a.cs;
-    const int W = nwe * WPW;  // worker slots per CTA
+    const int W = nwe * WPW;  // worker slots per CTA (<= 32)
     const int rpc = int(a.rows_per_cluster);
     const SmemLayout L(sizeof(TQ), sizeof(TS), W, P, S, rpc);
     TQ *stage_base = reinterpret_cast<TQ *>(smem);
-    double *xbd = reinterpret_cast<double *>(smem + L.off_xbd);   // [2][rpc]  FP64 xbar
-    float2 *xbf = reinterpret_cast<float2 *>(smem + L.off_xbf);   // [2][rpc]  double-float xbar
-    TS *red = reinterpret_cast<TS *>(smem + L.off_red);           // [2][R][32]
-    uint64_t *sloc = reinterpret_cast<uint64_t *>(smem + L.off_sloc);  // [NX][8][R]
-    float2 *xbn = reinterpret_cast<float2 *>(smem + L.off_xbn);   // [2][R] (double-float path)
-    double *xbn_d = reinterpret_cast<double *>(smem + L.off_xbn);  // [2][R] (FP64 / generic path)
+    double *xbd = reinterpret_cast<double *>(smem + L.off_xb);  // [2][rpc] FP64 xbar
+    float2 *xbf = reinterpret_cast<float2 *>(smem + L.off_xb);  // [2][rpc] double-float xbar (same bytes)
+    TS *dsh = reinterpret_cast<TS *>(smem + L.off_d);           // [2][R][32]  w_i[j] from the first product
+    TS *coefs = reinterpret_cast<TS *>(smem + L.off_coef);      // [2][32][R]  coefficients of the second product
+    uint64_t *sloc = reinterpret_cast<uint64_t *>(smem + L.off_sloc);  // [NX][8][R] cluster row sums
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bars);  // [S]
     uint64_t *xchg = full + S;                                          // [NX]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // warps [0, nwe) stream Q; warp nwe + r owns row r of each group (row sums,
-    // cluster exchange, master update); lane 0 of warp nwe + 1 issues the TMA copies
+    // Warps [0, nwe) stream Q (both products).  Warp nwe + r ("control warp r")
+    // owns row r of each group: lane s handles worker slot s -- the machines'
+    // updates, the CTA row sum, the cluster exchange, the master's update and
+    // the second product's coefficients.  Lane 0 of control warp 1 issues TMA.
     const bool is_ctl = warp >= nwe;
     const int ctl_r = warp - nwe;
     const int issuer = (nwe + 1) * 32;
@@ -286,24 +290,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     const float2 c_em = make_float2(a.em_hi, a.em_lo);  // eta / m
     const float2 c_1e = make_float2(a.e1_hi, a.e1_lo);  // 1 - eta
 
-    // byte offsets of this lane's Q vectors within a stage: [slot][row][vector]
-    uint32_t qoff[WPW][R][H];
-#pragma unroll
-    for (int sl = 0; sl < WPW; ++sl)
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int h = 0; h < H; ++h)
-                qoff[sl][r][h] = uint32_t((r * L.row_stride + (warp * WPW + sl) * P + (h * 32 + lane) * V) * sizeof(TQ));
-    const uint32_t stage_bytes = uint32_t(L.stage_elems * sizeof(TQ));
-    const unsigned char *stage_bytes_base = smem;
-
-    // element warps: lane (r_l, s_l) updates row r_l of worker slot s_l
-    const int r_l = lane >> 4, s_l = lane & 15;
-    const bool upd_lane = !is_ctl && s_l < WPW;
-    const int wl_upd = warp * WPW + s_l;  // CTA-local worker slot
-    const bool upd_active = upd_lane && wl_upd < W_cta;
-
     if (tid == 0) {
         abort_flag = 0;
         abort_code = 0;
@@ -318,8 +304,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     }
     // Zero the stage ring once: rows past the end of a group and worker slots
     // past the CTA's last worker are never written by TMA, so the element loops
-    // below read finite values there and need no per-row or per-slot guards
-    // (their results are discarded or multiplied by zero).
+    // read finite values there and need no guards (their results are discarded
+    // or multiplied by a zero coefficient).
     {
         uint4 *p = reinterpret_cast<uint4 *>(smem);
         const size_t n16 = size_t(S) * L.stage_elems * sizeof(TQ) / 16;
@@ -347,10 +333,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     };
     if (tid == issuer && W_cta > 0 && G > 0) {
         policy = policy_evict_first();
-        while (issued < min(int64_t(S - 3), total)) issue_next();
+        while (issued < min(int64_t(S - 4), total)) issue_next();
     }
 
-    // z_i (this pass's input) and the partial z_i' (output), per worker slot
+    // ---- element warps: z_i (this pass's input) and the partial z_i' (output) ----
     TC z[WPW][CPL], acc[WPW][CPL];
     auto load_z = [&](int64_t t) {
         const TS *zin = zbuf + size_t(t % 3) * mP + size_t(w0) * P;
@@ -368,162 +354,213 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         }
     };
     load_z(a.t0);
+    // byte offsets of this lane's Q vectors within a stage: [slot][row][vector]
+    uint32_t qoff[WPW][R][H];
+#pragma unroll
+    for (int sl = 0; sl < WPW; ++sl)
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+                qoff[sl][r][h] = uint32_t((r * L.row_stride + (warp * WPW + sl) * P + (h * 32 + lane) * V) * sizeof(TQ));
+    const uint32_t stage_bytes = uint32_t(L.stage_elems * sizeof(TQ));
+    // element lane (r_l, s_l) publishes w_i of row r_l of worker slot warp*WPW + s_l
+    const int r_l = lane >> 4, s_l = lane & 15;
+    const bool d_lane = !is_ctl && s_l < WPW;
+    const int wl_d = warp * WPW + s_l;
 
-    // previous x_i of (row r_l, slot s_l) of pass-local group k, loaded ahead
-    auto xload = [&](int k) -> TS {
-        if (!rx || !upd_active) return TS(0);
-        const int li = k * R + r_l;
-        return li < nrows ? xw[size_t(row0 + li) * m + wl_upd] : TS(0);
+    // ---- control warps: x_i of (row ctl_r, slot lane), one group ahead ----
+    const bool c_act = is_ctl && lane < W_cta;
+    TS *const cx0 = xw + size_t(row0 + (ctl_r & 1)) * m + lane;
+    const size_t xstep = size_t(R) * m;
+    const bool cx_ok = rx && c_act;
+    TS *cx_next = cx0;
+    int k_next = 0;
+    auto cx_load_next = [&]() -> TS {
+        TS v = TS(0);
+        if (cx_ok && k_next * R + ctl_r < nrows) v = *cx_next;
+        if (++k_next == G) {
+            k_next = 0;
+            cx_next = cx0;
+        } else {
+            cx_next += xstep;
+        }
+        return v;
     };
-    TS xpre = G > 0 ? xload(0) : TS(0);
-    TS x1 = TS(0), x2 = TS(0);  // this lane's x_i' of groups t-1 and t-2
-    int nr1 = 0, nr2 = 0;       // row counts of groups t-1 and t-2
-    int st1 = 0, ph1 = 0;       // stage / parity of the next first-product group
-    int st2 = 0;                // stage of the next second-product group
+    TS cxpre = (is_ctl && G > 0) ? cx_load_next() : TS(0);
+    TS *cx_cur = cx0;
+    TS xh0 = TS(0), xh1 = TS(0), xh2 = TS(0);  // this lane's x_i' of groups t, t-1, t-2
+    int nrh1 = 0, nrh2 = 0;                     // row counts of groups t-1, t-2
+
+    uint32_t sb1 = 0, sb2 = 0;  // stage byte offsets: first product (group t), second (group t-3)
+    int st1 = 0, ph1 = 0;
+    int gpass = 0;              // global index of group 0 of the current pass
     int cur = 0;
 
-    for (int64_t it = 0; it < a.iters; ++it) {
-        const int64_t gbase = it * G;
-        for (int t = 0; t < G + DELAY && G > 0; ++t) {
-            const bool has1 = t < G, has2 = t >= DELAY;
-            const int nr = has1 ? min(R, nrows - t * R) : 0;
-            const int64_t g = gbase + t;   // global index of group t (first product)
-            const int64_t g2 = g - DELAY;  // global index of group t-2 (second product)
-            TS xn_cur = TS(0);
-
-            if (!is_ctl) {
-                // ---- first product and machines' updates of group t ----
-                if (has1) {
-                    if (W_cta > 0 && !mbar_wait(&full[st1], uint32_t(ph1), a.timeout_ns)) {
-                        abort_flag = 1;
-                        abort_code = DEV_TIMEOUT_TMA;
-                    }
-                    const unsigned char *stb = stage_bytes_base + uint32_t(st1) * stage_bytes;
-                    TC dsum[WPW];
-#pragma unroll
-                    for (int sl = 0; sl < WPW; ++sl) {
-                        TC dr[R];
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            TC d0 = TC(0), d1 = TC(0);
-#pragma unroll
-                            for (int h = 0; h < H; ++h) {
-                                TC qv[V];
-                                load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
-                                dot_vec<TC, V>(d0, d1, qv, &z[sl][h * V]);
-                            }
-                            dr[r] = d0 + d1;
-                        }
-                        // transposed butterfly: lanes 0-15 end with row 0, lanes 16-31 with row 1
-                        TC keep = (lane & 16) ? dr[1] : dr[0];
-                        const TC send = (lane & 16) ? dr[0] : dr[1];
-                        keep += __shfl_xor_sync(0xffffffffu, send, 16);
-#pragma unroll
-                        for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
-                        dsum[sl] = keep;
-                    }
-                    TC myd = dsum[0];
-#pragma unroll
-                    for (int sl = 1; sl < WPW; ++sl) myd = (s_l == sl) ? dsum[sl] : myd;
-                    TS contrib = TS(0);
-                    if (upd_active && r_l < nr) {
-                        const int li = t * R + r_l;
-                        if constexpr (kDF) {
-                            const float2 xb = xbf[cur * rpc + li];
-                            const float xo = xpre;
-                            const float v = ((xb.x - xo) + xb.y) - myd;
-                            xn_cur = axpy_exact(xo, g_hi, g_lo, v);
-                            contrib = xn_cur;
-                        } else {
-                            double xn, cb;
-                            Row::update(mode, double(xpre), xbd[cur * rpc + li], double(myd), a.gamma, a.eta,
-                                        a.inv_m, xn, cb);
-                            xn_cur = TS(xn);
-                            contrib = (mode == MODE_APC || mode == MODE_INIT) ? xn_cur : TS(cb);
-                        }
-                        if (wx) xw[size_t(row0 + li) * m + wl_upd] = xn_cur;
-                    }
-                    if (upd_lane) red[((int(g) & 1) * R + r_l) * 32 + wl_upd] = contrib;
-                    // x_i of the next group, loaded after the store above (with one
-                    // group per pass the next group is the same rows)
-                    xpre = xload(t + 1 < G ? t + 1 : 0);
-                }
-            } else if (has2 && ctl_r < R && lane == 0) {
-                // ---- master of row ctl_r of group t-2: cluster row sums -> new xbar ----
-                const int r = ctl_r;
-                const int bx = int(g2 & (NX - 1));
-                if (!mbar_wait(&xchg[bx], uint32_t((g2 >> 2) & 1), a.timeout_ns)) {
+    // Step t: first product of group t; master and coefficients of group t-2
+    // (control warps); second product of group t-3.  Returns true on a timeout.
+    auto step = [&](int t) -> bool {
+        const bool e1 = t < G, mm = t >= 2 && t - 2 < G, e2 = t >= 3;
+        const int g = gpass + t;
+        const int nr = e1 ? min(R, nrows - t * R) : 0;
+        if (!is_ctl) {
+            if (e1) {
+                if (W_cta > 0 && !mbar_wait(&full[st1], uint32_t(ph1), a.timeout_ns)) {
                     abort_flag = 1;
-                    abort_code = DEV_TIMEOUT_XCHG;
+                    abort_code = DEV_TIMEOUT_TMA;
                 }
-                if (r < nr2) {
-                    const int li = (t - DELAY) * R + r;
-                    if constexpr (kDF) {
-                        float2 Ssum = make_float2(0.0f, 0.0f);
-                        for (int kk = 0; kk < cs; ++kk) {
-                            const uint64_t w = sloc[(bx * 8 + kk) * R + r];
-                            Ssum = df_add(Ssum, make_float2(__uint_as_float(uint32_t(w)), __uint_as_float(uint32_t(w >> 32))));
+                const unsigned char *stb = smem + sb1;
+                TC dsum[WPW];
+#pragma unroll
+                for (int sl = 0; sl < WPW; ++sl) {
+                    TC dr[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        TC d0 = TC(0), d1 = TC(0);
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            TC qv[V];
+                            load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
+                            dot_vec<TC, V>(d0, d1, qv, &z[sl][h * V]);
                         }
-                        const float2 xnew = df_add(df_mul(c_em, Ssum), df_mul(c_1e, xbf[cur * rpc + li]));
-                        xbf[(cur ^ 1) * rpc + li] = xnew;
-                        xbn[(int(g2) & 1) * R + r] = xnew;
-                    } else {
-                        double Ssum = 0.0;
-                        for (int kk = 0; kk < cs; ++kk) {
-                            const uint64_t w = sloc[(bx * 8 + kk) * R + r];
-                            if constexpr (kF64) Ssum += __longlong_as_double(static_cast<long long>(w));
-                            else Ssum += double(__uint_as_float(uint32_t(w))) + double(__uint_as_float(uint32_t(w >> 32)));
-                        }
-                        const double xnew = Row::master(mode, Ssum, xbd[cur * rpc + li], a.gamma, a.eta, a.inv_m);
-                        xbd[(cur ^ 1) * rpc + li] = xnew;
-                        xbn_d[(int(g2) & 1) * R + r] = xnew;
+                        dr[r] = d0 + d1;
                     }
+                    // transposed butterfly: lanes 0-15 end with row 0, lanes 16-31 with row 1
+                    TC keep = (lane & 16) ? dr[1] : dr[0];
+                    const TC send = (lane & 16) ? dr[0] : dr[1];
+                    keep += __shfl_xor_sync(0xffffffffu, send, 16);
+#pragma unroll
+                    for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
+                    dsum[sl] = keep;
+                }
+                TC myd = dsum[0];
+#pragma unroll
+                for (int sl = 1; sl < WPW; ++sl) myd = (s_l == sl) ? dsum[sl] : myd;
+                if (d_lane) dsh[((g & 1) * R + r_l) * 32 + wl_d] = myd;
+            }
+        }
+
+        if (__syncthreads_or(abort_flag)) return true;
+
+        if (!is_ctl) {
+            if (e2) {
+                // ---- second product of group t-3: z_i' += Q_i[j,:]^T coef_i[j] ----
+                const int g3 = g - 3;
+                const unsigned char *stb = smem + sb2;
+#pragma unroll
+                for (int sl = 0; sl < WPW; ++sl) {
+                    const TS *cp = coefs + ((g3 & 1) * 32 + warp * WPW + sl) * R;
+                    TC cr[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) cr[r] = cp[r];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h) {
+                            TC qv[V];
+                            load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
+                            axpy_vec<TC, V>(&acc[sl][h * V], qv, cr[r]);
+                        }
+                    }
+                }
+                sb2 += stage_bytes;
+                if (sb2 == uint32_t(S) * stage_bytes) sb2 = 0;
+            }
+            if (e1 && ++st1 == S) {
+                st1 = 0;
+                ph1 ^= 1;
+            }
+            sb1 = uint32_t(st1) * stage_bytes;
+        } else if (ctl_r < R) {
+            const int r = ctl_r;
+            if (e1 && tid == issuer && W_cta > 0 && issued < total) issue_next();
+            if (mm) {
+                // ---- master of row r of group t-2: cluster row sums -> new xbar, coefficients ----
+                const int g2 = g - 2;
+                const int bx = g2 & (NX - 1);
+                const int li = (t - 2) * R + r;
+                if constexpr (kDF) {
+                    float2 xnew = make_float2(0.0f, 0.0f);
+                    if (lane == 0) {
+                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> 2) & 1), a.timeout_ns)) {
+                            abort_flag = 1;
+                            abort_code = DEV_TIMEOUT_XCHG;
+                        }
+                        if (r < nrh2) {
+                            float2 Ssum = make_float2(0.0f, 0.0f);
+                            for (int kk = 0; kk < cs; ++kk) {
+                                const uint64_t w = sloc[(bx * 8 + kk) * R + r];
+                                Ssum = df_add(Ssum, make_float2(__uint_as_float(uint32_t(w)),
+                                                                __uint_as_float(uint32_t(w >> 32))));
+                            }
+                            xnew = df_add(df_mul(c_em, Ssum), df_mul(c_1e, xbf[cur * rpc + li]));
+                            xbf[(cur ^ 1) * rpc + li] = xnew;
+                        }
+                    }
+                    xnew.x = __shfl_sync(0xffffffffu, xnew.x, 0);
+                    xnew.y = __shfl_sync(0xffffffffu, xnew.y, 0);
+                    const TS c = (r < nrh2 && lane < W_cta) ? TS((xnew.x - float(xh2)) + xnew.y) : TS(0);
+                    coefs[((g2 & 1) * 32 + lane) * R + r] = c;
+                } else {
+                    double xnew = 0.0;
+                    if (lane == 0) {
+                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> 2) & 1), a.timeout_ns)) {
+                            abort_flag = 1;
+                            abort_code = DEV_TIMEOUT_XCHG;
+                        }
+                        if (r < nrh2) {
+                            double Ssum = 0.0;
+                            for (int kk = 0; kk < cs; ++kk) {
+                                const uint64_t w = sloc[(bx * 8 + kk) * R + r];
+                                if constexpr (kF64) Ssum += __longlong_as_double(static_cast<long long>(w));
+                                else Ssum += double(__uint_as_float(uint32_t(w))) +
+                                             double(__uint_as_float(uint32_t(w >> 32)));
+                            }
+                            xnew = Row::master(mode, Ssum, xbd[cur * rpc + li], a.gamma, a.eta, a.inv_m);
+                            xbd[(cur ^ 1) * rpc + li] = xnew;
+                        }
+                    }
+                    xnew = __shfl_sync(0xffffffffu, xnew, 0);
+                    const TS c = (r < nrh2 && lane < W_cta)
+                                     ? TS(Row::coef(mode, double(xh2), xnew, a.eta, a.inv_m)) : TS(0);
+                    coefs[((g2 & 1) * 32 + lane) * R + r] = c;
                 }
             }
-
-            if (__syncthreads_or(abort_flag)) goto abort_exit;
-
-            if (!is_ctl) {
-                // ---- second product of group t-2: z_i' += Q_i[j,:]^T coef_i[j] ----
-                if (has2) {
-                    const unsigned char *stb = stage_bytes_base + uint32_t(st2) * stage_bytes;
-                    TC myc = TC(0);
-                    if (upd_active && r_l < nr2) {
-                        if constexpr (kDF) {
-                            const float2 xb = xbn[(int(g2) & 1) * R + r_l];
-                            myc = (xb.x - x2) + xb.y;
-                        } else {
-                            myc = TC(Row::coef(mode, double(x2), xbn_d[(int(g2) & 1) * R + r_l], a.eta, a.inv_m));
-                        }
+            if (e1) {
+                // ---- machines' updates of row r of group t and the CTA row sum ----
+                TS xn = TS(0), contrib = TS(0);
+                if (r < nr && c_act) {
+                    const int li = t * R + r;
+                    const TS d = dsh[((g & 1) * R + r) * 32 + lane];
+                    if constexpr (kDF) {
+                        const float2 xb = xbf[cur * rpc + li];
+                        const float xo = cxpre;
+                        const float v = ((xb.x - xo) + xb.y) - d;
+                        xn = axpy_exact(xo, g_hi, g_lo, v);
+                        contrib = xn;
+                    } else {
+                        double xnd, cb;
+                        Row::update(mode, double(cxpre), xbd[cur * rpc + li], double(d), a.gamma, a.eta, a.inv_m,
+                                    xnd, cb);
+                        xn = TS(xnd);
+                        contrib = (mode == MODE_APC || mode == MODE_INIT) ? xn : TS(cb);
                     }
-#pragma unroll
-                    for (int sl = 0; sl < WPW; ++sl) {
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const TC cr = __shfl_sync(0xffffffffu, myc, r * 16 + sl);
-#pragma unroll
-                            for (int h = 0; h < H; ++h) {
-                                TC qv[V];
-                                load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
-                                axpy_vec<TC, V>(&acc[sl][h * V], qv, cr);
-                            }
-                        }
-                    }
+                    if (wx) *cx_cur = xn;
                 }
-            } else if (has1 && ctl_r < R) {
-                if (tid == issuer && W_cta > 0 && issued < total) issue_next();
-                // ---- this CTA's sum of row ctl_r of group t, sent to every CTA of the cluster ----
-                const int r = ctl_r;
-                const int bx = int(g & (NX - 1));
+                // x_i of the next group, loaded after the store above (with one
+                // group per pass the next group is the same rows)
+                cxpre = cx_load_next();
+                cx_cur = (t + 1 < G) ? cx_cur + xstep : cx0;
+                xh0 = xn;
+                const int bx = g & (NX - 1);
                 uint64_t payload;
                 if constexpr (kF64) {
-                    double v = (lane < W) ? double(red[((int(g) & 1) * R + r) * 32 + lane]) : 0.0;
+                    double v = double(contrib);
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
                     payload = uint64_t(__double_as_longlong(v));
                 } else {
-                    float sv = (lane < W) ? float(red[((int(g) & 1) * R + r) * 32 + lane]) : 0.0f;
-                    float cv = 0.0f;
+                    float sv = float(contrib), cv = 0.0f;
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) {
                         const float so = __shfl_xor_sync(0xffffffffu, sv, off);
@@ -546,17 +583,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                     mbar_arrive_expect_tx(&xchg[bx], r < nr ? uint32_t((cs - 1) * 8) : 0u);
                 }
             }
-            if (has2 && ++st2 == S) st2 = 0;
-            if (has1 && ++st1 == S) {
-                st1 = 0;
-                ph1 ^= 1;
-            }
-            // shift this lane's per-group history: group t becomes t-1, t-1 becomes t-2
-            x2 = x1;
-            x1 = xn_cur;
-            nr2 = nr1;
-            nr1 = nr;
+            // this lane's history: group t becomes t-1, t-1 becomes t-2
+            xh2 = xh1;
+            xh1 = e1 ? xh0 : TS(0);
+            xh0 = TS(0);
+            nrh2 = nrh1;
+            nrh1 = nr;
         }
+        return false;
+    };
+
+    for (int64_t it = 0; it < a.iters; ++it) {
+        cx_cur = cx0;
+        for (int t = 0; t < G + 3 && G > 0; ++t)
+            if (step(t)) goto abort_exit;
+        gpass += G;
 
         // ---- end of pass: publish z', clear the spare buffer, grid barrier ----
         {
@@ -601,6 +642,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         }
     }
 
+    // a wait that ran out in the last step is reported like any other
+    if (__syncthreads_or(abort_flag)) goto abort_exit;
     // the master's estimate for this cluster's rows
     if (rank == 0) {
         for (int i = tid; i < nrows; i += blockDim.x) {
