@@ -51,6 +51,7 @@ __all__ = [
     "relative_residual", "relative_error", "invariant_drift",
     "rate_apc", "rate_cimmino", "rate_consensus", "convergence_time",
     "apc_forward_linear", "apc_adjoint", "power_mu_max", "ApcTrace",
+    "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine",
 ]
 
 
@@ -369,3 +370,57 @@ def power_mu_max(Qs, v0: np.ndarray, iters: int) -> float:
         v = w / np.linalg.norm(w)
     w = sum(Q @ (Q.T @ v) for Q in Qs) / m
     return float(v @ w)
+
+
+# ---------------------------------------------------------------------------
+# The affine form of the machines' update (App. A), used with stored bases
+# ---------------------------------------------------------------------------
+
+def round_bf16(a) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16 (8 significant bits, the
+    exponent range of IEEE single), ties to even, and return them as float64.
+
+    Definition written out: a = f * 2^e with 0.5 <= |f| < 1 (``frexp``); the
+    nearest value with 8 significant bits is rint(f * 2^8) * 2^(e - 8), where
+    ``rint`` rounds half-way cases to the even integer.  Values here are far
+    from the overflow and subnormal ranges, which this definition does not
+    treat."""
+    a = np.asarray(a, dtype=np.float64)
+    f, e = np.frexp(a)
+    return np.ldexp(np.rint(np.ldexp(f, 8)), e - 8)
+
+
+def block_coefficients(Q_i: np.ndarray, R_i: np.ndarray, b_i: np.ndarray) -> np.ndarray:
+    """c_i = R_i^{-T} b_i, the coordinates of the least-norm solution in the
+    basis Q_i: x_i(0) = Q_i c_i and Q_i^T x = c_i for every solution x of
+    A_i x = b_i (A_i^T = Q_i R_i, Sec. 3.3).  Works for k right-hand sides."""
+    return sla.solve_triangular(R_i, b_i, trans="T", lower=False)
+
+
+def apc_step_affine(xs, xbar, Qs, cs, gamma: float, eta: float):
+    """One iteration in the form of App. A, Eq. (e_i(t+1)) written for x:
+        x_i(t+1) = (1 - gamma) x_i(t) + gamma (P_i xbar(t) + Q_i c_i),
+        xbar(t+1) = (eta/m) sum_i x_i(t+1) + (1 - eta) xbar(t),
+    with P_i y = y - Q_i (Q_i^T y).  App. A derives it from Eq. (cons1) using
+    only that x_i(t) solves A_i x = b_i, i.e. P_i x_i = x_i - Q_i c_i; so with an
+    orthonormal Q_i and iterates that keep that invariant the two forms give
+    the same sequence.  With a rounded (not exactly orthonormal) basis they
+    differ, and this is the form to compare against."""
+    m = len(xs)
+    new_xs = []
+    for x_i, Q_i, c_i in zip(xs, Qs, cs):
+        P_xbar = xbar - Q_i @ (Q_i.T @ xbar)
+        new_xs.append((1.0 - gamma) * x_i + gamma * (P_xbar + Q_i @ c_i))
+    new_xbar = (eta / m) * sum(new_xs) + (1.0 - eta) * xbar
+    return new_xs, new_xbar
+
+
+def apc_run_affine(Qs, cs, gamma: float, eta: float, T: int):
+    """Algorithm 1 with the affine step: x_i(0) = Q_i c_i, xbar(0) the mean of
+    the x_i(0), then T applications of ``apc_step_affine``.  Returns
+    (xs(T), xbar(T))."""
+    xs = [Q @ c for Q, c in zip(Qs, cs)]
+    xbar = sum(xs) / len(xs)
+    for _ in range(T):
+        xs, xbar = apc_step_affine(xs, xbar, Qs, cs, gamma, eta)
+    return xs, xbar
