@@ -1,0 +1,110 @@
+/*
+ * apc_batch.h -- C ABI of the batched APC solver: many independent systems
+ * A_s X_s = B_s (s = 0 .. nsys-1), each square (n_s x n_s) with its own
+ * uneven row partition and k <= 32 right-hand sides, advanced together by one
+ * persistent kernel on the tensor cores.
+ *
+ * Method per system (Azizan-Ruhi, Lahouti, Avestimehr, Hassibi, 2017): the
+ * rows are split into m_s contiguous blocks (Sec. 2), each block keeps an
+ * iterate x_i (n x k) and the master keeps xbar (n x k).  One iteration is
+ *     z_i  = Q_i^T xbar - c_i,
+ *     x_i <- x_i + gamma_s (xbar - x_i - Q_i z_i)                  (cons1)
+ *     xbar <- (eta_s/m_s) sum_i x_i + (1 - eta_s) xbar              (cons2)
+ * where Q_i is an orthonormal basis of the row space of A_i (Sec. 3.3) and
+ * c_i = R_i^{-T} b_i the coordinates of every solution of A_i x = b_i in it,
+ * so that Q_i z_i = Q_i Q_i^T (xbar - x_i) = (I - P_i)(xbar - x_i): this is
+ * Eq. (cons1) in the form used in App. A (Eq. (e_i(t+1)), which relies on
+ * A_i x_i = b_i).  Initialisation (Algorithm 1): x_i(0) = Q_i c_i, the
+ * least-norm solution of A_i x = b_i, and xbar(0) their mean.
+ *
+ * Arithmetic: set-up in FP64 (Cholesky QR per block, as apc_setup); Q_i is
+ * stored in BF16; the iterates are FP32, the master's estimate double-float,
+ * and products accumulate in FP32 on the tensor cores.
+ *
+ * Conventions are those of apc.h: APC_OK or a negative APC_ERR_* code; *_dev
+ * pointers are device memory, *_host host memory; the caller owns every
+ * buffer it passes; `stream` is a cudaStream_t passed as void*; a batch
+ * belongs to the device current at apc_batch_setup; calls on one batch must
+ * not overlap.  Matrices are row-major.
+ */
+#ifndef APC_BATCH_H
+#define APC_BATCH_H
+
+#include "apc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct apc_batch apc_batch;
+
+/* apc_batch_setup -- partition and factor every system (Sec. 2, Sec. 3.3) and
+ * form the least-norm coordinates c_i of every right-hand side.
+ *   n_host[s], m_host[s] : size and number of row blocks of system s.
+ *   row_offsets_host     : the systems' offsets one after another, m_s + 1
+ *                          int64 each (0 = first, n_s = last), blocks of 1..256
+ *                          rows and fewer rows than n_s, m_s <= 256.
+ *   A_dev_host[s]        : host array of device pointers, A_s n_s x n_s FP64,
+ *                          leading dimension n_s.
+ *   B_dev_host[s]        : host array of device pointers, B_s n_s x k FP64,
+ *                          leading dimension k.  Copied.
+ *   k                    : right-hand sides per system, 1..32.
+ *   opt                  : NULL or precision APC_BF16 (the only one) and the
+ *                          limit of every device-side wait (0 = 2 s).
+ * Errors: INVALID_ARG, UNSUPPORTED (k, precision), SINGULAR_BLOCK, NONFINITE,
+ * NOMEM, LAUNCH, CUDA; the text names the system.  On error *out is NULL. */
+int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const int32_t *m_host,
+                    const int64_t *row_offsets_host, const double *const *A_dev_host,
+                    const double *const *B_dev_host, int32_t k, const apc_options *opt, void *stream);
+
+/* apc_batch_set_params -- (gamma_s, eta_s) per system, host arrays of nsys
+ * (Theorem 1 gives the optimal pair from the extreme eigenvalues of X_s, see
+ * apc_optimal_params).  Errors: PARAMS unless 0 < gamma_s < 2 and eta_s is
+ * finite (nothing is changed then), INVALID_ARG, CUDA. */
+int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *eta_host);
+
+/* apc_batch_reset -- Algorithm 1 initialisation of every system.  With
+ * B_dev_host non-NULL the right-hand sides are replaced first (same layout
+ * as in apc_batch_setup).  Errors: INVALID_ARG, TIMEOUT, CUDA. */
+int apc_batch_reset(apc_batch *b, const double *const *B_dev_host, void *stream);
+
+/* apc_batch_iterate -- `iters` iterations of every system in one persistent
+ * launch, replayed from a CUDA graph captured once per iteration count.
+ * Synchronises the stream to read the device error flag.  Errors: PARAMS
+ * (no apc_batch_set_params yet), INVALID_ARG (no reset yet, iters < 0),
+ * TIMEOUT, CUDA. */
+int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream);
+
+/* apc_batch_get_xbar -- the master's estimate of system s as FP64,
+ * n_s x k row-major with leading dimension ldx >= k, into X_dev.
+ * apc_batch_get_x -- the iterate x_i of machine `worker` of system s, same
+ * layout.  Errors: INVALID_ARG, CUDA. */
+int apc_batch_get_xbar(apc_batch *b, int32_t sys, double *X_dev, int64_t ldx, void *stream);
+int apc_batch_get_x(apc_batch *b, int32_t sys, int32_t worker, double *X_dev, int64_t ldx, void *stream);
+
+/* apc_batch_set_test_hooks -- failure injection for tests, as
+ * apc_set_test_hooks: every grid barrier of later launches waits for
+ * grid_barrier_skew arrivals more than the grid has, and every device-side
+ * wait gives up after timeout_s seconds (0 = 2 s).  A launch then returns
+ * APC_ERR_TIMEOUT and the batch stays usable (reset, then iterate).
+ * Errors: INVALID_ARG. */
+int apc_batch_set_test_hooks(apc_batch *b, int32_t grid_barrier_skew, double timeout_s);
+
+/* apc_batch_info -- sizes: systems, right-hand sides, bytes of the packed
+ * BF16 bases, bytes of the machines' iterates, CTAs of the persistent grid
+ * and the work units of its two sweeps.  Any pointer may be NULL. */
+int apc_batch_info(const apc_batch *b, int32_t *nsys, int32_t *k, int64_t *q_bytes, int64_t *state_bytes,
+                   int32_t *grid, int32_t *units_a, int32_t *units_b);
+
+/* apc_batch_last_error -- text of the last error on b (or of the last failed
+ * apc_batch_setup when b is NULL). */
+const char *apc_batch_last_error(const apc_batch *b);
+
+/* apc_batch_destroy -- free the batch and its device buffers.  NULL is a no-op. */
+void apc_batch_destroy(apc_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* APC_BATCH_H */

@@ -1,4 +1,4 @@
-"""Thin ctypes binding of the C ABI in ``include/apc.h``.
+"""Thin ctypes binding of the C ABI in ``include/apc.h`` and ``include/apc_batch.h``.
 
 Argument marshalling only: every step of the solver runs in the CUDA library
 ``_build/libapc.so``.  PyTorch supplies device memory (tensors are passed by
@@ -26,6 +26,8 @@ ERRORS = {
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
     "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
+    "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
+    "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
 )
 
 
@@ -78,8 +80,22 @@ def lib() -> C.CDLL:
     L.apc_last_error.restype = C.c_char_p
     L.apc_destroy.argtypes = [vp]
     L.apc_destroy.restype = None
+    L.apc_batch_setup.argtypes = [C.POINTER(vp), i32, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
+                                  C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(apc_options), vp]
+    L.apc_batch_set_params.argtypes = [vp, C.POINTER(dbl), C.POINTER(dbl)]
+    L.apc_batch_reset.argtypes = [vp, vp, vp]
+    L.apc_batch_iterate.argtypes = [vp, i64, vp]
+    L.apc_batch_get_xbar.argtypes = [vp, i32, vp, i64, vp]
+    L.apc_batch_get_x.argtypes = [vp, i32, i32, vp, i64, vp]
+    L.apc_batch_set_test_hooks.argtypes = [vp, i32, dbl]
+    L.apc_batch_info.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i64),
+                                 C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    L.apc_batch_last_error.argtypes = [vp]
+    L.apc_batch_last_error.restype = C.c_char_p
+    L.apc_batch_destroy.argtypes = [vp]
+    L.apc_batch_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("apc_last_error", "apc_destroy"):
+        if name not in ("apc_last_error", "apc_destroy", "apc_batch_last_error", "apc_batch_destroy"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -274,3 +290,128 @@ def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0,
                              offs.ctypes.data_as(C.POINTER(C.c_int64)), m, C.byref(opt), _stream(stream))
     _check(rc, None)
     return Context(h, A.device, offs)
+
+
+def _check_batch(rc: int, handle=None):
+    if rc != 0:
+        msg = lib().apc_batch_last_error(handle).decode(errors="replace")
+        raise ApcError(rc, msg)
+
+
+class Batch:
+    """Owns an ``apc_batch``: independent square systems advanced together."""
+
+    def __init__(self, handle: C.c_void_p, device, n, k, B):
+        self.handle = handle
+        self.device = device
+        self.n = list(n)
+        self.k = k
+        self._B = B  # the caller's right-hand sides (kept alive for reset)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def close(self):
+        if self.handle:
+            lib().apc_batch_destroy(self.handle)
+            self.handle = None
+
+    def info(self) -> dict:
+        ns, k, grid, ua, ub = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        qb, sb = C.c_int64(), C.c_int64()
+        _check_batch(lib().apc_batch_info(self.handle, C.byref(ns), C.byref(k), C.byref(qb), C.byref(sb),
+                                          C.byref(grid), C.byref(ua), C.byref(ub)), self.handle)
+        return {"nsys": ns.value, "k": k.value, "q_bytes": qb.value, "state_bytes": sb.value,
+                "grid": grid.value, "units_a": ua.value, "units_b": ub.value}
+
+    def set_params(self, gammas, etas):
+        import numpy as np
+        g = np.ascontiguousarray(np.asarray(gammas, dtype=np.float64))
+        e = np.ascontiguousarray(np.asarray(etas, dtype=np.float64))
+        if g.shape != (len(self.n),) or e.shape != (len(self.n),):
+            raise ValueError("one gamma and one eta per system")
+        _check_batch(lib().apc_batch_set_params(self.handle, g.ctypes.data_as(C.POINTER(C.c_double)),
+                                                e.ctypes.data_as(C.POINTER(C.c_double))), self.handle)
+
+    def reset(self, B=None, stream=None):
+        arr = None
+        if B is not None:
+            B = [_batch_rhs(b_, n_, self.k) for b_, n_ in zip(B, self.n)]
+            arr = (C.c_void_p * len(B))(*[b_.data_ptr() for b_ in B])
+            self._B = B
+        with _device(self.device):
+            _check_batch(lib().apc_batch_reset(self.handle, arr, _stream(stream)), self.handle)
+
+    def iterate(self, iters: int, stream=None):
+        with _device(self.device):
+            _check_batch(lib().apc_batch_iterate(self.handle, int(iters), _stream(stream)), self.handle)
+
+    def xbar(self, s: int, stream=None):
+        import torch
+        out = torch.empty((self.n[s], self.k), dtype=torch.float64, device=self.device)
+        with _device(self.device):
+            _check_batch(lib().apc_batch_get_xbar(self.handle, s, _ptr(out), self.k, _stream(stream)), self.handle)
+        return out
+
+    def x(self, s: int, worker: int, stream=None):
+        import torch
+        out = torch.empty((self.n[s], self.k), dtype=torch.float64, device=self.device)
+        with _device(self.device):
+            _check_batch(lib().apc_batch_get_x(self.handle, s, worker, _ptr(out), self.k, _stream(stream)),
+                         self.handle)
+        return out
+
+    def set_test_hooks(self, grid_barrier_skew: int = 0, timeout_s: float = 0.0):
+        _check_batch(lib().apc_batch_set_test_hooks(self.handle, int(grid_barrier_skew), float(timeout_s)),
+                     self.handle)
+
+
+def _device(dev):
+    import torch
+    return torch.cuda.device(dev)
+
+
+def _batch_rhs(B, n, k):
+    import torch
+    if not B.is_cuda or B.dtype != torch.float64:
+        raise TypeError("float64 CUDA tensors expected")
+    B = B.reshape(n, k) if B.dim() == 1 else B
+    if tuple(B.shape) != (n, k):
+        raise ValueError(f"right-hand side of shape {tuple(B.shape)}, expected {(n, k)}")
+    return B.contiguous()
+
+
+def apc_batch_setup(As, Bs, row_offsets, timeout_s=0.0, stream=None) -> Batch:
+    """Factor every system: As[s] an n_s x n_s FP64 CUDA tensor, Bs[s] its
+    n_s x k right-hand sides (k equal for all systems, <= 32), row_offsets[s]
+    its m_s + 1 block offsets."""
+    import numpy as np
+    import torch
+    nsys = len(As)
+    if nsys < 1 or len(Bs) != nsys or len(row_offsets) != nsys:
+        raise ValueError("one A, one B and one offset list per system")
+    ns = [int(A.shape[0]) for A in As]
+    k = int(Bs[0].shape[1]) if Bs[0].dim() == 2 else 1
+    for A in As:
+        if not A.is_cuda or A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+            raise TypeError("square float64 CUDA matrices expected")
+    As = [A.contiguous() for A in As]
+    Bs = [_batch_rhs(B, n_, k) for B, n_ in zip(Bs, ns)]
+    offs = [np.asarray(o, dtype=np.int64) for o in row_offsets]
+    n_arr = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    m_arr = np.ascontiguousarray(np.asarray([len(o) - 1 for o in offs], dtype=np.int32))
+    o_arr = np.ascontiguousarray(np.concatenate(offs))
+    a_arr = (C.c_void_p * nsys)(*[A.data_ptr() for A in As])
+    b_arr = (C.c_void_p * nsys)(*[B.data_ptr() for B in Bs])
+    opt = apc_options(APC_BF16, 0, 0, float(timeout_s))
+    h = C.c_void_p()
+    with torch.cuda.device(As[0].device):
+        rc = lib().apc_batch_setup(C.byref(h), nsys, n_arr.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   m_arr.ctypes.data_as(C.POINTER(C.c_int32)),
+                                   o_arr.ctypes.data_as(C.POINTER(C.c_int64)), a_arr, b_arr, k, C.byref(opt),
+                                   _stream(stream))
+    _check_batch(rc, None)
+    return Batch(h, As[0].device, ns, k, Bs)

@@ -22,7 +22,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["gaussian_system", "scaled_system", "batch_systems", "even_offsets",
-           "uneven_offsets", "target_vector", "gaussian_system_torch", "scaled_system_torch"]
+           "uneven_offsets", "target_vector", "gaussian_system_torch", "scaled_system_torch",
+           "batch_specs", "batch_systems_torch"]
 
 
 def even_offsets(N: int, m: int) -> np.ndarray:
@@ -106,3 +107,31 @@ def scaled_system_torch(n: int, seed: int, device, lo: float = 2.0, hi: float = 
     A.mul_(d_r[:, None]).mul_(d_c[None, :])
     x_true = torch.randn((n,), generator=g, device=device, dtype=torch.float64)
     return A, x_true, A @ x_true
+
+
+def batch_specs(nsys: int, seed: int, n_lo: int = 256, n_hi: int = 4096, p_lo: int = 16, p_hi: int = 128):
+    """Sizes and row partitions of ``nsys`` independent systems: n ~ U{n_lo..n_hi},
+    block sizes p_i ~ U{p_lo..p_hi} (the last block truncated).  Host-side draw,
+    cheap at any size; the matrices come from ``batch_systems_torch``."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    for _ in range(nsys):
+        n = int(rng.integers(n_lo, n_hi + 1))
+        specs.append((n, uneven_offsets(n, p_lo, p_hi, rng)))
+    return specs
+
+
+def batch_systems_torch(specs, seed: int, device, k: int = 32):
+    """(As, Bs, offsets) on the device for ``batch_specs``: A = G + 0.5 sqrt(n) I
+    with G i.i.d. N(0,1), B n x k i.i.d. N(0,1), FP64."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    As, Bs, offs = [], [], []
+    for n, o in specs:
+        A = torch.randn((n, n), generator=g, device=device, dtype=torch.float64)
+        A.diagonal().add_(0.5 * float(np.sqrt(n)))
+        As.append(A)
+        Bs.append(torch.randn((n, k), generator=g, device=device, dtype=torch.float64))
+        offs.append(o)
+    return As, Bs, offs
