@@ -18,6 +18,10 @@ Also on the same JSON line:
                Gaussian system (2304 x 2048, 9 blocks of 256, kappa(X) ~ 1e3): the
                32768 scaled matrix has kappa(X) ~ 1e12 and needs far more
                iterations than a benchmark can run;
+  batch        the batched solver on 256 independent systems (n ~ U{256..4096},
+               A = G + 0.5 sqrt(n) I, blocks p_i ~ U{16..128}, k = 32
+               right-hand sides, BF16 bases): iterations per second of the
+               whole batch and its roofline (HBM bytes and tensor-pipe work);
   cpu_baseline the FP64 oracle timed on a bounded sample (8 of the 128 blocks).
 
 `--impl reference` times the FP64 CPU oracle alone on the same workload (the
@@ -283,6 +287,52 @@ def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
         c32.close()
 
 
+def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None):
+    """The batched solver (one persistent launch of `iters` iterations per
+    step) on the 256-system workload.  Algorithmic bytes per iteration: the
+    packed BF16 bases read twice (one product each) and the machines'
+    iterates read and written once."""
+    import numpy as np
+    import torch
+    from paper_1708_01413_gb300 import apc, inputs
+    specs = inputs.batch_specs(nsys, seed=2024)
+    As, Bs, offs = inputs.batch_systems_torch(specs, seed=2024, device=dev, k=k)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bt = apc.apc_batch_setup(As, Bs, offs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del As, Bs
+    info = bt.info()
+    bt.set_params([1.0] * nsys, [1.0] * nsys)  # in S for every system; the cost does not depend on them
+    bt.reset()
+    bt.iterate(iters)
+    torch.cuda.synchronize()
+    ev = [(_ev(), _ev()) for _ in range(reps)]
+    with (clocks if clocks is not None else ClockSampler(torch.cuda.current_device())) as clk:
+        for a, b_ in ev:
+            a.record(stream)
+            bt.iterate(iters)
+            b_.record(stream)
+        torch.cuda.synchronize()
+    sec = statistics.mean(a.elapsed_time(b_) for a, b_ in ev) / 1e3 / iters
+    alg = 2 * info["q_bytes"] + 2 * info["state_bytes"]
+    ns = np.array([n for n, _ in specs], dtype=np.float64)
+    kp = 16 if k <= 16 else 32
+    cq = info["q_bytes"] / 2.0  # sum over systems of npad * Cq
+    mma_flops = 2.0 * cq * kp * (2 + 3)  # both products, operands in 2 + 3 BF16 planes
+    bt.close()
+    achieved = alg / sec / 1e9
+    return {"workload": f"{nsys} systems, n ~ U{{256..4096}} (sum n^2 = {float((ns ** 2).sum()):.3g}), "
+                        f"A = G + 0.5 sqrt(n) I, blocks p_i ~ U{{16..128}}, k = {k}, BF16 bases",
+            "iter_per_s": 1.0 / sec, "ms_per_iter": sec * 1e3, "rhs_iter_per_s": nsys * k / sec,
+            "iters_per_launch": iters, "launches": reps, "setup_s": round(setup_s, 3), "grid": info["grid"],
+            "clocks": clk.summary(),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "algorithmic_bytes_per_iter": alg, "kernel": "apc_batch_kernel",
+                         "tensor_tflops": mma_flops / sec / 1e12}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -370,6 +420,11 @@ def run_ours(args):
             extra["fp32"] = time_fp32(A, b, offs, gamma, eta, T, peak, stream)
         except Exception as exc:  # a failed comparison must not lose the headline number
             extra["fp32"] = {"error": str(exc)}
+    if args.batch and rank == 0:
+        try:
+            extra["batch"] = time_batch(dev, peak, stream)
+        except Exception as exc:
+            extra["batch"] = {"error": str(exc)}
     if args.tts and rank == 0:
         try:
             extra["tts"] = time_to_tolerance(dev)
@@ -411,6 +466,24 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch_only(args):
+    """`--only batch`: the batched workload alone, one JSON line."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    peak, peak_kind = hbm_peak()
+    r = time_batch(dev, peak, torch.cuda.current_stream(), iters=args.batch_iters, reps=args.steps,
+                   nsys=args.batch_systems)
+    r["roofline"]["peak_kind"] = peak_kind
+    line = {"metric": "APC iterations/s of the whole batch (all systems, all right-hand sides)",
+            "value": r["iter_per_s"], "unit": "iter/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+            "ms_per_step": r["ms_per_iter"] * args.batch_iters, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": r["workload"], "iters_per_step": args.batch_iters,
+                       "l2": "bases and iterates >> L2 129 MB, no flush"},
+            "gpu_launches": args.steps, "roofline": r["roofline"], "clocks": r["clocks"], "batch": r}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -425,6 +498,11 @@ def main():
     p.add_argument("--fp32", type=int, default=1, help="also time the FP32 path on the same matrix")
     p.add_argument("--tts", type=int, default=1, help="also measure time to 1e-10 (BF16+IR vs FP32+IR)")
     p.add_argument("--e2e", type=int, default=1)
+    p.add_argument("--batch", type=int, default=1, help="also time the batched solver (256 systems, k = 32)")
+    p.add_argument("--only", default="all", choices=["all", "batch"],
+                   help="batch: time only the batched workload (for profiling)")
+    p.add_argument("--batch-systems", type=int, default=256)
+    p.add_argument("--batch-iters", type=int, default=50)
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
     if args.impl == "reference":
@@ -432,7 +510,10 @@ def main():
     else:
         from paper_1708_01413_gb300 import build
         build.build()
-        run_ours(args)
+        if args.only == "batch":
+            run_batch_only(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":
