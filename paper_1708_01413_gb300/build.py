@@ -34,7 +34,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     srcs = sources()
     deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    deps.append(os.path.join(os.path.dirname(HERE), "include", "apc.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    deps += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     if not force and os.path.exists(LIB):
         t_lib = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t_lib for d in deps):

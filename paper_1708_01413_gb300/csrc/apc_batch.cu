@@ -13,20 +13,30 @@
 // Y = Q^T xbar, over the packed basis Q = [Q_1 .. Q_m] (n x C).
 //
 // One iteration is two sweeps separated by grid barriers:
-//   sweep A  unit = (system, 256 rows); warp = 32 rows.  For every machine i:
-//            W^T = Z_i^T Q_i^T (mma.sync m16n8k16; A = Z_i^T split into two
-//            BF16 planes, B = the BF16 basis from shared memory), then the
-//            update of x_i and the running row sum; at the end the master's
-//            row update (double-float) and xbar' split into three BF16
-//            planes, stored in the A-fragment order of sweep B.
-//   sweep B  unit = (system, 512 columns); warp = 64 columns, all rows.
-//            Y^T = xbar'^T Q (A = xbar'^T in three planes, B = the basis via
+//   sweep A  unit = (system, tile of 256 rows); a consumer warp owns 32 rows.
+//            The packed columns are walked in 64-column windows; for every
+//            16-column chunk of machine i, W^T += Z_i^T Q_i^T (mma.sync
+//            m16n8k16; A = z_i split into two BF16 planes, B = the basis via
+//            ldmatrix), and after the machine's last chunk its update and the
+//            running row sum; at the end of the unit the master's row update
+//            (double-float) and xbar' split into three BF16 planes, stored in
+//            the A-fragment order of sweep B.
+//   sweep B  unit = (system, 512 columns); a consumer warp owns 64 columns,
+//            all rows: Y^T = xbar'^T Q (A = the planes, B = the basis via
 //            ldmatrix.trans), then Z = Y - c split into two planes, stored in
 //            the A-fragment order of sweep A.
 // The accumulator fragment of one sweep is, lane for lane, the operand
-// fragment of the other, so no transposes are needed.  The basis is staged
-// through a 4-deep cp.async ring of XOR-swizzled tiles.  Units are assigned
-// to CTAs on the host, longest first (LPT).
+// fragment of the other, so no transposes are needed.
+//
+// Data movement.  The basis is stored tile-major and pre-swizzled: for each
+// 256-row tile and 64-column window a contiguous [rows][64] BF16 block whose
+// 16-byte chunks are XOR-permuted by (row & 7), the order ldmatrix reads
+// without bank conflicts.  A machine's x_i tile is likewise one contiguous
+// block ([k][rows + 8] FP32).  So every stage is one or a few 1-D TMA bulk
+// copies, issued by a producer warp into a ring of 4 basis slots and 2 x_i
+// slots; 8 consumer warps wait on the slots' mbarriers (bounded waits) and
+// release them with per-warp arrivals, so no CTA-wide barrier sits in the
+// streaming loop.  Units are assigned to CTAs on the host, longest first.
 //
 // Precision: Q_i is BF16 (rounded once from the FP64 QR); products accumulate
 // in FP32 on the tensor cores; an operand split into planes keeps 16 (sweep
@@ -55,32 +65,37 @@ namespace {
 
 using namespace apc;
 
-constexpr int kThreads = 256;
-constexpr int kRowsA = 256;        // rows of a sweep-A unit (32 per warp)
-constexpr int kColsStageA = 64;    // basis columns per sweep-A stage
-constexpr int kColsB = 512;        // columns of a sweep-B unit (64 per warp)
-constexpr int kRowsStageB = 32;    // rows per sweep-B stage
-constexpr int kStages = 4;         // cp.async ring depth
+constexpr int kConsumerWarps = 8;
+constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+constexpr int kTileRows = 256;   // rows of a sweep-A unit (32 per consumer warp)
+constexpr int kWin = 64;         // basis columns per sweep-A window (one 128-byte row)
+constexpr int kColsB = 512;      // columns of a sweep-B unit (64 per consumer warp)
+constexpr int kRowsStageB = 32;  // rows per sweep-B stage
+constexpr int kQSlots = 4, kXSlots = 2;
 constexpr int kPlanesA = 2, kPlanesB = 3;
-constexpr int kStageQBytes = 32768;  // 256 x 64 or 32 x 512 BF16
-constexpr int kStageBytes = 40960;   // basis tile + operand planes
-constexpr size_t kSmemBytes = size_t(kStages) * kStageBytes;
+constexpr int kSlotQBytes = kTileRows * kWin * 2;  // 32 KB: 256 x 64 or 8 x (32 x 64) BF16
+constexpr int kSlotZBytes = 8192;                  // operand planes of one stage
+constexpr int kSlotBytes = kSlotQBytes + kSlotZBytes;
+constexpr int kXPad = 8;                           // FP32 padding per right-hand-side row of an x_i tile
+constexpr int kXSlotBytes = 32 * (kTileRows + kXPad) * 4;
+constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
+constexpr size_t kSmemBytes = size_t(kBarOffset) + 2 * (kQSlots + kXSlots) * sizeof(uint64_t);
 
 struct SysDesc {
-    const __nv_bfloat16 *Q;  // [npad][Cq], zero outside the blocks
-    float *X;                // [m][kp][npad]   machines' iterates, transposed
-    float2 *Xb;              // [kp][npad]      master estimate, double-float
+    const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
+    float *X;                // tile-major x_i blocks (see x_block)
+    float2 *Xb;              // [kp][npad]  master estimate, double-float
     uint4 *Xfrag;            // [npad/16][MT][kPlanesB][32]  xbar' operand planes
     uint2 *Zfrag;            // [Cq/8][MT][kPlanesA][32]     z operand planes
     const float4 *Cfrag;     // [Cq/8][MT][32]               c_i, FP32
-    const int *coloff;       // [m + 1], multiples of 8
-    int npad, m, Cq, pad;
+    const int *coloff;       // [m + 1], multiples of 16
+    int npad, m, Cq, C;
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo, im_hi, im_lo;
 };
 
 struct BatchArgs {
     const SysDesc *sys;
-    const int2 *unitsA;  // (system, first row)
+    const int2 *unitsA;  // (system, first row of the tile)
     const int *offA;     // [grid + 1]
     const int2 *unitsB;  // (system, first column)
     const int *offB;     // [grid + 1]
@@ -92,15 +107,18 @@ struct BatchArgs {
     uint64_t timeout_ns;
 };
 
+// rows of tile t
+__host__ __device__ __forceinline__ int tile_rows(int npad, int t) { return min(kTileRows, npad - kTileRows * t); }
+// first element of the basis block (tile t, window w): [tile_rows][64] BF16
+__host__ __device__ __forceinline__ size_t q_block(int Cq, int npad, int t, int w) {
+    return size_t(t) * kTileRows * Cq + size_t(w) * tile_rows(npad, t) * kWin;
+}
+// first element of machine i's x_i block in tile t: [kp][tile_rows + kXPad] FP32
+__host__ __device__ __forceinline__ size_t x_block(int m, int kp, int npad, int t, int i) {
+    return size_t(t) * m * kp * (kTileRows + kXPad) + size_t(i) * kp * (tile_rows(npad, t) + kXPad);
+}
+
 // ---- PTX wrappers ------------------------------------------------------------
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
@@ -116,13 +134,24 @@ __device__ __forceinline__ void lds128(uint32_t addr, uint32_t (&v)[4]) {
     asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
                  : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(addr));
 }
-// D += A B, m16n8k16, BF16 operands, FP32 accumulators
+// D += A B, m16n8k16, BF16 operands, FP32 accumulators.  Not volatile: the
+// compiler may interleave independent accumulations (a chain of MMAs on one
+// accumulator would otherwise wait out the pipe latency at every step).
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
+    asm(
         "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// pull [src, src + bytes) into L2 ahead of its bulk copy into shared memory
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+// order this thread's generic-proxy global writes before later async-proxy
+// (bulk copy) reads of them
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // ---- arithmetic ----------------------------------------------------------------
@@ -170,419 +199,460 @@ __device__ __forceinline__ float2 dfm(float2 a, float2 b) {
     return make_float2(hi, e - (hi - p));
 }
 
-// Bounded grid barrier: false when the wait ran out of time.
-__device__ bool grid_barrier(uint32_t *bar, uint32_t target, uint64_t timeout_ns, int *abort_flag) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        red_release_add_u32(bar, 1u);
-        if (ld_acquire_u32(bar) < target) {
-            const uint64_t t0 = globaltimer_ns();
-            while (ld_acquire_u32(bar) < target) {
-                if (globaltimer_ns() - t0 > timeout_ns) {
-                    *abort_flag = 1;
-                    break;
-                }
-            }
-        }
-        __threadfence();
+// ---- the ring ------------------------------------------------------------------
+struct Ring {
+    uint8_t *smem;
+    uint64_t *full, *empty, *xfull, *xempty;  // [kQSlots], [kQSlots], [kXSlots], [kXSlots]
+    int *abort_flag;
+    uint64_t timeout_ns;
+
+    __device__ uint8_t *qslot(int s) const { return smem + size_t(s) * kSlotBytes; }
+    __device__ uint8_t *xslot(int s) const { return smem + size_t(kQSlots) * kSlotBytes + size_t(s) * kXSlotBytes; }
+    // one non-blocking poll of a phase
+    __device__ static bool test(uint64_t *bar, uint32_t parity) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        return ok != 0;
     }
-    return !__syncthreads_or(*abort_flag);
+    // Bounded wait on a phase, spinning on test_wait (a suspended try_wait
+    // wakes up late enough to cost a quarter of the sweep time); on time-out
+    // raise the CTA's abort flag.
+    __device__ bool wait(uint64_t *bar, uint32_t parity) const {
+        if (*reinterpret_cast<volatile int *>(abort_flag)) return false;
+        if (test(bar, parity)) return true;
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 <= timeout_ns)
+            if (test(bar, parity)) return true;
+        atomicExch(abort_flag, 1);
+        return false;
+    }
+    __device__ bool aborted() const { return *reinterpret_cast<volatile int *>(abort_flag) != 0; }
+};
+
+// Cursor over the stages of the ring, kept identically by the producer and by
+// every consumer warp: stage q uses slot q % S with phase parity (q / S) & 1.
+struct Cursor {
+    uint32_t q = 0, x = 0;
+};
+
+// Producer: wait until slot of stage q is free (its previous use consumed).
+__device__ __forceinline__ bool acquire_slot(const Ring &R, uint64_t *empty, int S, uint32_t q) {
+    if (q < uint32_t(S)) return true;
+    return R.wait(&empty[q % S], ((q / S) - 1) & 1);
 }
 
-// ---- sweep A: machines' first product, update, master ----------------------------
+// ---- sweep A ---------------------------------------------------------------------
 template <int MT>
-struct SweepA {
-    static constexpr int KP = 16 * MT;
-    const SysDesc d;
-    const int row0, rows, tid, warp, lane, g, t;
-    const bool wact;
-    const uint32_t sbase;
-    int pi, ps, pc0, pw16;  // producer cursor: worker, sub-stage, its columns
-
-    __device__ SweepA(const SysDesc &d_, int row0_, uint32_t sbase_)
-        : d(d_), row0(row0_), rows(min(kRowsA, d_.npad - row0_)), tid(threadIdx.x), warp(threadIdx.x >> 5),
-          lane(threadIdx.x & 31), g((threadIdx.x & 31) >> 2), t(threadIdx.x & 3),
-          wact(32 * int(threadIdx.x >> 5) < min(kRowsA, d_.npad - row0_)), sbase(sbase_), pi(0), ps(0) {
-        load_worker(0, pc0, pw16);
-    }
-
-    // first column and width (rounded up to 16) of worker i
-    __device__ void load_worker(int i, int &c0, int &w16) const {
-        if (i < d.m) {
-            c0 = __ldg(d.coloff + i);
-            w16 = (__ldg(d.coloff + i + 1) - c0 + 15) & ~15;
-        } else {
-            c0 = 0;
-            w16 = 0;
+__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init,
+                                 uint64_t policy) {
+    constexpr int KP = 16 * MT;
+    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    const int nwin = d.Cq / kWin;
+    const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = 8 * MT * kPlanesA * 256;
+    const uint32_t xbytes = uint32_t(KP) * (rows + kXPad) * 4;
+    int pi = 0;  // next machine whose x_i tile is due
+    // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory ring
+    constexpr int kPrefetch = 4;
+    for (int w = 0; w < min(kPrefetch, nwin); ++w) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w), qbytes);
+    if (!init)
+        for (int j = 0; j < min(kPrefetch, d.m); ++j) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, j), xbytes);
+    for (int w = 0; w < nwin; ++w) {
+        const uint32_t s = cur.q % kQSlots;
+        if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
+        mbar_arrive_expect_tx(&R.full[s], qbytes + zbytes);
+        tma_load_1d(R.qslot(s), d.Q + q_block(d.Cq, d.npad, t, w), qbytes, &R.full[s], policy);
+        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Zfrag + size_t(8 * w) * MT * kPlanesA * 32, zbytes, &R.full[s],
+                    policy);
+        if (w + kPrefetch < nwin) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w + kPrefetch), qbytes);
+        ++cur.q;
+        // x_i tiles of the machines whose last chunk lies in this window
+        while (!init && pi < d.m && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
+            const uint32_t xs = cur.x % kXSlots;
+            if (!acquire_slot(R, R.xempty, kXSlots, cur.x)) return;
+            mbar_arrive_expect_tx(&R.xfull[xs], xbytes);
+            tma_load_1d(R.xslot(xs), d.X + x_block(d.m, KP, d.npad, t, pi), xbytes, &R.xfull[xs], policy);
+            if (pi + kPrefetch < d.m) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, pi + kPrefetch), xbytes);
+            ++cur.x;
+            ++pi;
         }
     }
+}
 
-    // Issue the next stage into ring slot `slot` (an empty group past the end).
-    __device__ void issue(int slot) {
-        if (pi < d.m) {
-            const int cs = pc0 + kColsStageA * ps;
-            const int nch = min(kColsStageA, pw16 - kColsStageA * ps) >> 3;  // 16-byte chunks per row
-            const uint32_t sq = sbase + slot * kStageBytes;
-            const __nv_bfloat16 *src = d.Q + size_t(row0) * d.Cq + cs;
+template <int MT>
+__device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init, float gh,
+                                 float gl) {
+    constexpr int KP = 16 * MT;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    const bool wact = 32 * warp < rows;
+    const int wrow = row0 + 32 * warp;  // first row of this warp
+    const int nwin = d.Cq / kWin, nchunk = d.C / 16;
+    const int xstride = rows + kXPad;   // floats per right-hand side in an x_i tile
+    float xbh[MT][4][4], xbl[MT][4][4], S[MT][4][4], acc[MT][4][4];
+    // accumulator element e of (mt, nt): right-hand side 16 mt + g + 8 (e >> 1),
+    // row wrow + 8 nt + 2 tq + (e & 1)
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int idx = tid + kThreads * k;
-                const int r = idx >> 3, ch = idx & 7;
-                if (ch < nch && r < rows)
-                    cp_async16(sq + r * 128 + ((ch ^ (r & 7)) << 4), src + size_t(r) * d.Cq + 8 * ch);
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                S[mt][nt][e] = 0.0f;
+                acc[mt][nt][e] = 0.0f;
+                xbh[mt][nt][e] = 0.0f;
+                xbl[mt][nt][e] = 0.0f;
             }
-            const int zchunks = nch * MT * kPlanesA * 16;  // 16-byte pieces of the z planes
-            const uint8_t *zsrc = reinterpret_cast<const uint8_t *>(d.Zfrag + size_t(cs >> 3) * MT * kPlanesA * 32);
-            for (int idx = tid; idx < zchunks; idx += kThreads)
-                cp_async16(sq + kStageQBytes + idx * 16, zsrc + size_t(idx) * 16);
-            if (++ps * kColsStageA >= pw16) {
-                ps = 0;
-                ++pi;
-                load_worker(pi, pc0, pw16);
-            }
-        }
-        cp_async_commit();
-    }
-
-    __device__ void run(bool init, float gh, float gl) {
-        float xbh[MT][4][4], xbl[MT][4][4], S[MT][4][4], acc[MT][4][4], xr[MT][4][4];
-        const int wrow = row0 + 32 * warp;
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    S[mt][nt][e] = 0.0f;
-                    acc[mt][nt][e] = 0.0f;
-                    xbh[mt][nt][e] = 0.0f;
-                    xbl[mt][nt][e] = 0.0f;
-                    xr[mt][nt][e] = 0.0f;
-                }
-        // accumulator element e of (mt, nt): rhs 16 mt + g + 8 (e >> 1),
-        // row wrow + 8 nt + 2 t + (e & 1)
-        if (wact && !init) {
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int rhs = 16 * mt + g + 8 * h;
-                        const float4 v = __ldcg(reinterpret_cast<const float4 *>(
-                            d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * t));  // {hi, lo} of two rows
-                        xbh[mt][nt][2 * h] = v.x;
-                        xbl[mt][nt][2 * h] = v.y;
-                        xbh[mt][nt][2 * h + 1] = v.z;
-                        xbl[mt][nt][2 * h + 1] = v.w;
-                    }
-        }
-        for (int s = 0; s < kStages - 1; ++s) issue(s);
-        int ci = 0, cs = 0, cc0, cw16;
-        load_worker(0, cc0, cw16);
-        int slot = 0;
-        while (ci < d.m) {
-            cp_async_wait<kStages - 2>();
-            __syncthreads();
-            issue((slot + kStages - 1) % kStages);
-            const uint32_t sq = sbase + slot * kStageBytes, sz = sq + kStageQBytes;
-            const int width = min(kColsStageA, cw16 - kColsStageA * cs);
-            const bool first = cs == 0, last = (cs + 1) * kColsStageA >= cw16;
-            // an odd number of 8-column groups: the second half of the last
-            // 16-column chunk holds the next block's columns and gets zero weight
-            const bool odd_tail = last && (((__ldg(d.coloff + ci + 1) - cc0) >> 3) & 1);
-            if (wact) {
-                if (first && !init) {
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const int rhs = 16 * mt + g + 8 * h;
-                                const float2 v = __ldcg(reinterpret_cast<const float2 *>(
-                                    d.X + (size_t(ci) * KP + rhs) * d.npad + wrow + 8 * nt + 2 * t));
-                                xr[mt][nt][2 * h] = v.x;
-                                xr[mt][nt][2 * h + 1] = v.y;
-                            }
-                }
-                const int nkc = width >> 4;
-                for (int kc = 0; kc < nkc; ++kc) {
-                    uint32_t a[MT][kPlanesA][4];
-                    const bool zero_hi = odd_tail && kc == nkc - 1;
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int p = 0; p < kPlanesA; ++p) {
-                            lds64(sz + (((2 * kc) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][0],
-                                  a[mt][p][1]);
-                            if (zero_hi) {
-                                a[mt][p][2] = 0u;
-                                a[mt][p][3] = 0u;
-                            } else {
-                                lds64(sz + (((2 * kc + 1) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][2],
-                                      a[mt][p][3]);
-                            }
-                        }
-                    uint32_t b[4][2];
-#pragma unroll
-                    for (int ntp = 0; ntp < 4; ntp += 2) {
-                        const int q = lane >> 3, r = lane & 7;
-                        const int row = 32 * warp + 8 * (ntp + (q >> 1)) + r;
-                        const int ch = 2 * kc + (q & 1);
-                        ldsm_x4(sq + row * 128 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
-                                b[ntp + 1][1]);
-                    }
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int p = 0; p < kPlanesA; ++p) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
-                }
-                if (last) {
-                    // x_i <- x_i + gamma (xbar - x_i - w_i); row sums over machines
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                float xn[2];
-#pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    const int e = 2 * h + u;
-                                    const float x = xr[mt][nt][e];
-                                    const float v = ((xbh[mt][nt][e] - x) + xbl[mt][nt][e]) - acc[mt][nt][e];
-                                    xn[u] = upd_exact(x, gh, gl, v);
-                                    S[mt][nt][e] += xn[u];
-                                    acc[mt][nt][e] = 0.0f;
-                                }
-                                const int rhs = 16 * mt + g + 8 * h;
-                                __stcg(reinterpret_cast<float2 *>(d.X + (size_t(ci) * KP + rhs) * d.npad + wrow +
-                                                                  8 * nt + 2 * t),
-                                       make_float2(xn[0], xn[1]));
-                            }
-                }
-            }
-            slot = (slot + 1) % kStages;
-            if (last) {
-                cs = 0;
-                ++ci;
-                load_worker(ci, cc0, cw16);
-            } else {
-                ++cs;
-            }
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-        if (!wact) return;
-        // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
-        const float2 em = make_float2(init ? d.im_hi : d.em_hi, init ? d.im_lo : d.em_lo);
-        const float2 e1 = make_float2(d.e1_hi, d.e1_lo);
-        float xo[MT][4][4];
+    if (wact && !init) {
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
             for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    float2 xn[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int e = 2 * h + u;
-                        xn[u] = dfm(em, make_float2(S[mt][nt][e], 0.0f));
-                        if (!init) xn[u] = dfa(xn[u], dfm(e1, make_float2(xbh[mt][nt][e], xbl[mt][nt][e])));
-                        xo[mt][nt][e] = xn[u].x;
-                    }
                     const int rhs = 16 * mt + g + 8 * h;
-                    __stcg(reinterpret_cast<float4 *>(d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * t),
-                           make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
+                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(
+                        d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq));  // {hi, lo} of two rows
+                    xbh[mt][nt][2 * h] = v.x;
+                    xbl[mt][nt][2 * h] = v.y;
+                    xbh[mt][nt][2 * h + 1] = v.z;
+                    xbl[mt][nt][2 * h + 1] = v.w;
                 }
-        // xbar' operand planes of sweep B: in the 16-row chunk kc of this warp,
-        // a0/a1 are n-tile 2kc (rhs g / g+8) and a2/a3 n-tile 2kc+1
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc)
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                uint32_t w0[kPlanesB], w1[kPlanesB], w2[kPlanesB], w3[kPlanesB];
-                split2<kPlanesB>(xo[mt][2 * kc][0], xo[mt][2 * kc][1], w0);
-                split2<kPlanesB>(xo[mt][2 * kc][2], xo[mt][2 * kc][3], w1);
-                split2<kPlanesB>(xo[mt][2 * kc + 1][0], xo[mt][2 * kc + 1][1], w2);
-                split2<kPlanesB>(xo[mt][2 * kc + 1][2], xo[mt][2 * kc + 1][3], w3);
-                const size_t kcg = size_t(wrow >> 4) + kc;
-#pragma unroll
-                for (int p = 0; p < kPlanesB; ++p)
-                    __stcg(d.Xfrag + ((kcg * MT + mt) * kPlanesB + p) * 32 + lane,
-                           make_uint4(w0[p], w1[p], w2[p], w3[p]));
-            }
     }
-};
-
-// ---- sweep B: second product Y^T = xbar'^T Q, then Z = Y - c -----------------------
-template <int MT>
-struct SweepB {
-    const SysDesc d;
-    const int col0, ncols, tid, warp, lane;
-    const bool wact;
-    const uint32_t sbase;
-    int pr;  // first row of the next stage to issue
-
-    __device__ SweepB(const SysDesc &d_, int col0_, uint32_t sbase_)
-        : d(d_), col0(col0_), ncols(min(kColsB, d_.Cq - col0_)), tid(threadIdx.x), warp(threadIdx.x >> 5),
-          lane(threadIdx.x & 31), wact(64 * int(threadIdx.x >> 5) < min(kColsB, d_.Cq - col0_)), sbase(sbase_),
-          pr(0) {}
-
-    __device__ void issue(int slot) {
-        if (pr < d.npad) {
-            const uint32_t sq = sbase + slot * kStageBytes;
-            const int nch = ncols >> 3;
-            const __nv_bfloat16 *src = d.Q + size_t(pr) * d.Cq + col0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int idx = tid + kThreads * k;
-                const int r = idx >> 6, ch = idx & 63;
-                if (ch < nch) cp_async16(sq + r * 1024 + ((ch ^ (r & 7)) << 4), src + size_t(r) * d.Cq + 8 * ch);
-            }
-            const int xchunks = 2 * MT * kPlanesB * 32;  // two 16-row chunks of 16-byte lane vectors
-            const uint8_t *xsrc = reinterpret_cast<const uint8_t *>(d.Xfrag + size_t(pr >> 4) * MT * kPlanesB * 32);
-            for (int idx = tid; idx < xchunks; idx += kThreads)
-                cp_async16(sq + kStageQBytes + idx * 16, xsrc + size_t(idx) * 16);
-            pr += kRowsStageB;
-        }
-        cp_async_commit();
-    }
-
-    __device__ void run() {
-        float acc[MT][8][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-        for (int s = 0; s < kStages - 1; ++s) issue(s);
-        int slot = 0;
-        for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
-            cp_async_wait<kStages - 2>();
-            __syncthreads();
-            issue((slot + kStages - 1) % kStages);
+    int i = 0, iend = __ldg(d.coloff + 1) >> 4;  // machine of the current chunk, its end chunk
+    for (int w = 0; w < nwin; ++w) {
+        const uint32_t s = cur.q % kQSlots;
+        if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
+        const uint32_t sq = smem_u32(R.qslot(s)), sz = sq + kSlotQBytes;
+#pragma unroll 1
+        for (int kc = 0; kc < 4; ++kc) {
+            const int c16 = 4 * w + kc;
+            if (c16 >= nchunk) break;
             if (wact) {
-                const uint32_t sq = sbase + slot * kStageBytes, sx = sq + kStageQBytes;
+                uint32_t a[MT][kPlanesA][4];
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                    uint32_t a[MT][kPlanesB][4];
+                for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int p = 0; p < kPlanesB; ++p)
-                            lds128(sx + ((kc * MT + mt) * kPlanesB + p) * 512 + lane * 16, a[mt][p]);
-                    uint32_t b[8][2];
-#pragma unroll
-                    for (int ntp = 0; ntp < 8; ntp += 2) {
-                        const int q = lane >> 3, r = lane & 7;
-                        const int row = 16 * kc + 8 * (q & 1) + r;
-                        const int ch = 8 * warp + ntp + (q >> 1);
-                        ldsm_x4_t(sq + row * 1024 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
-                                  b[ntp + 1][1]);
+                    for (int p = 0; p < kPlanesA; ++p) {
+                        lds64(sz + (((2 * kc) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][0], a[mt][p][1]);
+                        lds64(sz + (((2 * kc + 1) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][2],
+                              a[mt][p][3]);
                     }
+                uint32_t b[4][2];
 #pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-                            for (int p = 0; p < kPlanesB; ++p) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
+                for (int ntp = 0; ntp < 4; ntp += 2) {
+                    const int q = lane >> 3, r = lane & 7;
+                    const int row = 32 * warp + 8 * (ntp + (q >> 1)) + r;
+                    const int ch = 2 * kc + (q & 1);
+                    ldsm_x4(sq + row * 128 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
+                            b[ntp + 1][1]);
                 }
-            }
-            slot = (slot + 1) % kStages;
-        }
-        cp_async_wait<0>();
-        __syncthreads();
-        if (wact) store_z(acc, false);
-    }
-
-    // Z = Y - c into the sweep-A operand planes (zero_y: the initial z = -c)
-    __device__ void store_z(float (&acc)[MT][8][4], bool zero_y) const {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const size_t G = size_t(col0 >> 3) + 8 * warp + nt;
-                const float4 c = __ldg(d.Cfrag + (G * MT + mt) * 32 + lane);
-                const float y0 = zero_y ? 0.0f : acc[mt][nt][0], y1 = zero_y ? 0.0f : acc[mt][nt][1];
-                const float y2 = zero_y ? 0.0f : acc[mt][nt][2], y3 = zero_y ? 0.0f : acc[mt][nt][3];
-                uint32_t w01[kPlanesA], w23[kPlanesA];
-                split2<kPlanesA>(y0 - c.x, y1 - c.y, w01);
-                split2<kPlanesA>(y2 - c.z, y3 - c.w, w23);
 #pragma unroll
                 for (int p = 0; p < kPlanesA; ++p)
-                    __stcg(d.Zfrag + ((G * MT + mt) * kPlanesA + p) * 32 + lane, make_uint2(w01[p], w23[p]));
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
             }
+            if (c16 + 1 == iend) {
+                // machine i is complete: x_i <- x_i + gamma (xbar - x_i - w_i), row sums
+                uint32_t xs = 0, sx = 0;
+                if (!init) {
+                    xs = cur.x % kXSlots;
+                    if (!R.wait(&R.xfull[xs], (cur.x / kXSlots) & 1)) return;
+                    sx = smem_u32(R.xslot(xs));
+                }
+                if (wact) {
+                    float *xg = d.X + x_block(d.m, KP, d.npad, t, i);
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int rhs = 16 * mt + g + 8 * h;
+                                const int rr = 32 * warp + 8 * nt + 2 * tq;  // row within the tile
+                                uint32_t x0 = 0u, x1 = 0u;
+                                if (!init) lds64(sx + (rhs * xstride + rr) * 4, x0, x1);
+                                const float xo[2] = {__uint_as_float(x0), __uint_as_float(x1)};
+                                float xn[2];
+#pragma unroll
+                                for (int u = 0; u < 2; ++u) {
+                                    const int e = 2 * h + u;
+                                    const float v = ((xbh[mt][nt][e] - xo[u]) + xbl[mt][nt][e]) - acc[mt][nt][e];
+                                    xn[u] = upd_exact(xo[u], gh, gl, v);
+                                    S[mt][nt][e] += xn[u];
+                                    acc[mt][nt][e] = 0.0f;
+                                }
+                                __stcg(reinterpret_cast<float2 *>(xg + rhs * xstride + rr), make_float2(xn[0], xn[1]));
+                            }
+                }
+                if (!init) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&R.xempty[xs]);
+                    ++cur.x;
+                }
+                ++i;
+                if (i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[s]);
+        ++cur.q;
     }
-};
+    if (!wact) return;
+    // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
+    const float2 em = make_float2(init ? d.im_hi : d.em_hi, init ? d.im_lo : d.em_lo);
+    const float2 e1 = make_float2(d.e1_hi, d.e1_lo);
+    float xo[MT][4][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float2 xn[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = 2 * h + u;
+                    xn[u] = dfm(em, make_float2(S[mt][nt][e], 0.0f));
+                    if (!init) xn[u] = dfa(xn[u], dfm(e1, make_float2(xbh[mt][nt][e], xbl[mt][nt][e])));
+                    xo[mt][nt][e] = xn[u].x;
+                }
+                const int rhs = 16 * mt + g + 8 * h;
+                __stcg(reinterpret_cast<float4 *>(d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq),
+                       make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
+            }
+    // xbar' operand planes of sweep B: in the 16-row chunk kc of this warp,
+    // a0/a1 are n-tile 2kc (rhs g / g+8) and a2/a3 n-tile 2kc+1
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt) {
+            uint32_t w0[kPlanesB], w1[kPlanesB], w2[kPlanesB], w3[kPlanesB];
+            split2<kPlanesB>(xo[mt][2 * kc][0], xo[mt][2 * kc][1], w0);
+            split2<kPlanesB>(xo[mt][2 * kc][2], xo[mt][2 * kc][3], w1);
+            split2<kPlanesB>(xo[mt][2 * kc + 1][0], xo[mt][2 * kc + 1][1], w2);
+            split2<kPlanesB>(xo[mt][2 * kc + 1][2], xo[mt][2 * kc + 1][3], w3);
+            const size_t kcg = size_t(wrow >> 4) + kc;
+#pragma unroll
+            for (int p = 0; p < kPlanesB; ++p)
+                __stcg(d.Xfrag + ((kcg * MT + mt) * kPlanesB + p) * 32 + lane, make_uint4(w0[p], w1[p], w2[p], w3[p]));
+        }
+}
+
+// ---- sweep B -----------------------------------------------------------------------
+template <int MT>
+__device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, uint64_t policy) {
+    const int nwin = min(kColsB, d.Cq - col0) / kWin;
+    const uint32_t xbytes = 2 * MT * kPlanesB * 512;
+    for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
+        const uint32_t s = cur.q % kQSlots;
+        if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
+        const int t = r0 / kTileRows, rr = r0 % kTileRows;
+        mbar_arrive_expect_tx(&R.full[s], uint32_t(nwin) * kRowsStageB * kWin * 2 + xbytes);
+        for (int j = 0; j < nwin; ++j)
+            tma_load_1d(R.qslot(s) + j * (kRowsStageB * kWin * 2),
+                        d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin,
+                        kRowsStageB * kWin * 2, &R.full[s], policy);
+        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xfrag + size_t(r0 >> 4) * MT * kPlanesB * 32, xbytes, &R.full[s],
+                    policy);
+        ++cur.q;
+    }
+}
+
+template <int MT>
+__device__ void store_z(const SysDesc &d, int col0, float (&acc)[MT][8][4], bool zero_y) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const size_t G = size_t(col0 >> 3) + 8 * warp + nt;
+            const float4 c = __ldg(d.Cfrag + (G * MT + mt) * 32 + lane);
+            const float y0 = zero_y ? 0.0f : acc[mt][nt][0], y1 = zero_y ? 0.0f : acc[mt][nt][1];
+            const float y2 = zero_y ? 0.0f : acc[mt][nt][2], y3 = zero_y ? 0.0f : acc[mt][nt][3];
+            uint32_t w01[kPlanesA], w23[kPlanesA];
+            split2<kPlanesA>(y0 - c.x, y1 - c.y, w01);
+            split2<kPlanesA>(y2 - c.z, y3 - c.w, w23);
+#pragma unroll
+            for (int p = 0; p < kPlanesA; ++p)
+                __stcg(d.Zfrag + ((G * MT + mt) * kPlanesA + p) * 32 + lane, make_uint2(w01[p], w23[p]));
+        }
+}
+
+template <int MT>
+__device__ void sweep_b_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int col0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool wact = 64 * warp < min(kColsB, d.Cq - col0);
+    float acc[MT][8][4];
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+    for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
+        const uint32_t s = cur.q % kQSlots;
+        if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
+        if (wact) {
+            // this warp's 64 columns: a [32][64] block, chunks XOR-permuted by (row & 7)
+            const uint32_t sq = smem_u32(R.qslot(s)) + warp * (kRowsStageB * kWin * 2);
+            const uint32_t sx = smem_u32(R.qslot(s)) + kSlotQBytes;
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc) {
+                uint32_t a[MT][kPlanesB][4];
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int p = 0; p < kPlanesB; ++p)
+                        lds128(sx + ((kc * MT + mt) * kPlanesB + p) * 512 + lane * 16, a[mt][p]);
+                uint32_t b[8][2];
+#pragma unroll
+                for (int ntp = 0; ntp < 8; ntp += 2) {
+                    const int q = lane >> 3, r = lane & 7;
+                    const int row = 16 * kc + 8 * (q & 1) + r;
+                    const int ch = ntp + (q >> 1);
+                    ldsm_x4_t(sq + row * 128 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
+                              b[ntp + 1][1]);
+                }
+#pragma unroll
+                for (int p = 0; p < kPlanesB; ++p)
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[s]);
+        ++cur.q;
+    }
+    if (wact) store_z<MT>(d, col0, acc, false);
+}
+
+// Bounded grid barrier over all CTAs: false when the wait ran out of time.
+__device__ bool grid_barrier(uint32_t *bar, uint32_t target, uint64_t timeout_ns, int *abort_flag) {
+    fence_proxy_async_global();  // this sweep's global writes are read by bulk copies in the next
+    __syncthreads();
+    if (threadIdx.x == 0 && !*reinterpret_cast<volatile int *>(abort_flag)) {
+        __threadfence();
+        red_release_add_u32(bar, 1u);
+        if (ld_acquire_u32(bar) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            while (ld_acquire_u32(bar) < target) {
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicExch(abort_flag, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    return !__syncthreads_or(*reinterpret_cast<volatile int *>(abort_flag));
+}
 
 template <int MT>
 __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int abort_flag;
-    if (threadIdx.x == 0) abort_flag = 0;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
+    Ring R{smem, bars, bars + kQSlots, bars + 2 * kQSlots, bars + 2 * kQSlots + kXSlots, &abort_flag,
+           a.timeout_ns};
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool producer = warp == kConsumerWarps;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kQSlots; ++s) {
+            mbar_init(&R.full[s], 1);
+            mbar_init(&R.empty[s], kConsumerWarps);
+        }
+        for (int s = 0; s < kXSlots; ++s) {
+            mbar_init(&R.xfull[s], 1);
+            mbar_init(&R.xempty[s], kConsumerWarps);
+        }
+        fence_mbar_init_cluster();
+    }
     __syncthreads();
-    const uint32_t sbase = smem_u32(smem);
+    const uint64_t policy = policy_evict_first();
+    Cursor cur;
     uint32_t episode = 0;
     bool ok = true;
     if (a.init) {
         // z_i(0) = -c_i, so that sweep A with gamma = 1 and x = xbar = 0 forms
-        // the least-norm x_i(0) = Q_i c_i (Algorithm 1) and xbar(0) = their mean
-        for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1]; ++u) {
-            const int2 U = a.unitsB[u];
-            SweepB<MT> sb(a.sys[U.x], U.y, sbase);
-            if (sb.wact) {
-                float acc[MT][8][4] = {};
-                sb.store_z(acc, true);
+        // the least-norm x_i(0) = Q_i c_i (Algorithm 1) and xbar(0) their mean
+        if (!producer)
+            for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1]; ++u) {
+                const int2 U = a.unitsB[u];
+                const SysDesc &d = a.sys[U.x];
+                if (64 * warp < min(kColsB, d.Cq - U.y)) {
+                    float acc[MT][8][4] = {};
+                    store_z<MT>(d, U.y, acc, true);
+                }
             }
-        }
         ++episode;
         ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
     }
     for (int64_t it = 0; ok && it < a.iters; ++it) {
         const bool init = a.init && it == 0;
-        for (int u = a.offA[blockIdx.x]; u < a.offA[blockIdx.x + 1]; ++u) {
+        for (int u = a.offA[blockIdx.x]; u < a.offA[blockIdx.x + 1] && !R.aborted(); ++u) {
             const int2 U = a.unitsA[u];
-            SweepA<MT> sa(a.sys[U.x], U.y, sbase);
-            sa.run(init, init ? 1.0f : sa.d.g_hi, init ? 0.0f : sa.d.g_lo);
+            const SysDesc &d = a.sys[U.x];
+            if (producer) {
+                if (lane == 0) sweep_a_producer<MT>(R, cur, d, U.y, init, policy);
+            } else {
+                sweep_a_consumer<MT>(R, cur, d, U.y, init, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
+            }
         }
         ++episode;
         if (!(ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag))) break;
-        for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1]; ++u) {
+        for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1] && !R.aborted(); ++u) {
             const int2 U = a.unitsB[u];
-            SweepB<MT> sb(a.sys[U.x], U.y, sbase);
-            sb.run();
+            const SysDesc &d = a.sys[U.x];
+            if (producer) {
+                if (lane == 0) sweep_b_producer<MT>(R, cur, d, U.y, policy);
+            } else {
+                sweep_b_consumer<MT>(R, cur, d, U.y);
+            }
         }
         if (it + 1 < a.iters) {
             ++episode;
             ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
         }
     }
+    // no bulk copy may still be writing this CTA's shared memory at exit: the
+    // producer waits (bounded) for the last phase of every slot it filled
+    __syncthreads();
+    if (producer && lane == 0) {
+        for (uint32_t q = cur.q > uint32_t(kQSlots) ? cur.q - kQSlots : 0; q < cur.q; ++q)
+            (void)mbar_wait(&R.full[q % kQSlots], (q / kQSlots) & 1, a.timeout_ns);
+        for (uint32_t x = cur.x > uint32_t(kXSlots) ? cur.x - kXSlots : 0; x < cur.x; ++x)
+            (void)mbar_wait(&R.xfull[x % kXSlots], (x / kXSlots) & 1, a.timeout_ns);
+    }
+    __syncthreads();
     if (threadIdx.x == 0 && abort_flag) atomicCAS(a.err, 0, DEV_TIMEOUT_GRID);
 }
 
 // ---- set-up kernels -----------------------------------------------------------------
-// Qs [n][m][P] (single-system layout) -> Q [npad][Cq], block b at coloff[b]
+// Qs [n][m][P] (single-system layout) -> the tile-major, pre-swizzled packed
+// basis: element (row j, packed column col) of block b = colblk[col / 16].
 __global__ void repack_kernel(const __nv_bfloat16 *Qs, int64_t n, int m, int P, const int *colblk,
-                              const int *coloff, const int32_t *pcount, int64_t npad, int Cq, __nv_bfloat16 *Q) {
-    const int64_t total = npad * Cq;
+                              const int *coloff, const int32_t *pcount, int npad, int Cq, __nv_bfloat16 *Q) {
+    const int64_t total = int64_t(npad) * Cq;
     for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
          idx += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t j = idx / Cq;
-        const int cc = int(idx - j * Cq);
-        const int b = colblk[cc >> 3];
+        const int j = int(idx / Cq);
+        const int col = int(idx - int64_t(j) * Cq);
+        const int b = colblk[col >> 4];
         __nv_bfloat16 v = __float2bfloat16(0.0f);
         if (b >= 0 && j < n) {
-            const int c = cc - coloff[b];
+            const int c = col - coloff[b];
             if (c < pcount[b]) v = Qs[(size_t(j) * m + b) * P + c];
         }
-        Q[idx] = v;
+        const int t = j / kTileRows, r = j % kTileRows, w = col / kWin, cc = col % kWin;
+        Q[q_block(Cq, npad, t, w) + size_t(r) * kWin + (((cc >> 3) ^ (r & 7)) << 3) + (cc & 7)] = v;
     }
 }
 
@@ -627,13 +697,15 @@ __global__ void xbar_out_kernel(const float2 *Xb, int64_t n, int64_t npad, int k
     }
 }
 
-__global__ void x_out_kernel(const float *X, int64_t n, int64_t npad, int kp, int k, int worker, double *out,
+__global__ void x_out_kernel(const float *X, int64_t n, int npad, int m, int kp, int k, int worker, double *out,
                              int64_t ldx) {
     const int64_t total = n * k;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
-        const int64_t j = i / k;
-        const int r = int(i - j * k);
-        out[j * ldx + r] = double(X[(size_t(worker) * kp + r) * npad + j]);
+        const int j = int(i / k);
+        const int r = int(i - int64_t(j) * k);
+        const int t = j / kTileRows;
+        const size_t off = x_block(m, kp, npad, t, worker) + size_t(r) * (tile_rows(npad, t) + kXPad) + j % kTileRows;
+        out[int64_t(j) * ldx + r] = double(X[off]);
     }
 }
 
@@ -838,26 +910,30 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         b->ctx.push_back(c);
         b->n.push_back(n);
         b->m.push_back(m);
-        // packed column layout: block i at coloff[i], width rounded up to 8
+        // packed column layout: block i at coloff[i], width rounded up to 16
+        // (one k16 chunk never spans two blocks)
         std::vector<int> co(m + 1, 0);
-        for (int i = 0; i < m; ++i) co[i + 1] = co[i] + int((offs[i + 1] - offs[i] + 7) / 8 * 8);
+        for (int i = 0; i < m; ++i) co[i + 1] = co[i] + int((offs[i + 1] - offs[i] + 15) / 16 * 16);
         const int C = co[m];
-        const int Cq = (C + 8 + 63) / 64 * 64;
+        const int Cq = (C + kWin - 1) / kWin * kWin;
         const int64_t npad = (n + 31) / 32 * 32;
-        std::vector<int> colblk(Cq / 8, -1);
+        const int ntiles = int((npad + kTileRows - 1) / kTileRows);
+        std::vector<int> colblk(Cq / 16, -1);
         for (int i = 0; i < m; ++i)
-            for (int g8 = co[i] / 8; g8 < co[i + 1] / 8; ++g8) colblk[g8] = i;
+            for (int g16 = co[i] / 16; g16 < co[i + 1] / 16; ++g16) colblk[g16] = i;
         SysDesc d = {};
         d.npad = int(npad);
         d.m = m;
         d.Cq = Cq;
+        d.C = C;
+        const size_t x_elems = x_block(m, kp, int(npad), ntiles, 0);
         int *d_co = nullptr, *d_cb = nullptr;
         __nv_bfloat16 *Q = nullptr;
         float4 *Cf = nullptr;
         double *Bc = nullptr;
-        if ((rc = balloc(b, &d_co, sizeof(int) * (m + 1))) || (rc = balloc(b, &d_cb, sizeof(int) * (Cq / 8))) ||
+        if ((rc = balloc(b, &d_co, sizeof(int) * (m + 1))) || (rc = balloc(b, &d_cb, sizeof(int) * (Cq / 16))) ||
             (rc = balloc(b, &Q, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
-            (rc = balloc(b, &d.X, sizeof(float) * size_t(m) * kp * npad)) ||
+            (rc = balloc(b, &d.X, sizeof(float) * x_elems)) ||
             (rc = balloc(b, &d.Xb, sizeof(float2) * size_t(kp) * npad)) ||
             (rc = balloc(b, &d.Xfrag, sizeof(uint4) * size_t(npad / 16) * MT * kPlanesB * 32)) ||
             (rc = balloc(b, &d.Zfrag, sizeof(uint2) * size_t(Cq / 8) * MT * kPlanesA * 32)) ||
@@ -869,15 +945,15 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         d.coloff = d_co;
         b->B.push_back(Bc);
         b->q_bytes += int64_t(sizeof(__nv_bfloat16)) * npad * Cq;
-        b->state_bytes += int64_t(sizeof(float)) * m * kp * npad;
+        b->state_bytes += int64_t(sizeof(float)) * m * kp * npad;  // unpadded iterate bytes
         cudaMemcpyAsync(d_co, co.data(), sizeof(int) * (m + 1), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_cb, colblk.data(), sizeof(int) * (Cq / 8), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_cb, colblk.data(), sizeof(int) * (Cq / 16), cudaMemcpyHostToDevice, s);
         cudaMemcpyAsync(Bc, B_dev_host[sys], sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s);
-        cudaMemsetAsync(d.X, 0, sizeof(float) * size_t(m) * kp * npad, s);
+        cudaMemsetAsync(d.X, 0, sizeof(float) * x_elems, s);
         cudaMemsetAsync(d.Xb, 0, sizeof(float2) * size_t(kp) * npad, s);
         const unsigned grid = unsigned(std::min<int64_t>((npad * Cq + 255) / 256, 152 * 32));
         repack_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->Q), n, m, c->P, d_cb, d_co, c->d_p,
-                                           npad, Cq, Q);
+                                           int(npad), Cq, Q);
         if (cudaGetLastError() != cudaSuccess) {
             bfail(b, APC_ERR_CUDA, "repack launch failed");
             return bail(APC_ERR_CUDA);
@@ -923,8 +999,8 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
     std::vector<std::pair<double, int2>> ia, ib;
     for (int sys = 0; sys < nsys; ++sys) {
         const SysDesc &d = b->desc[sys];
-        for (int r0 = 0; r0 < d.npad; r0 += kRowsA) {
-            const int rows = std::min(kRowsA, d.npad - r0);
+        for (int r0 = 0; r0 < d.npad; r0 += kTileRows) {
+            const int rows = std::min(kTileRows, d.npad - r0);
             ia.push_back({double(rows) * (2.0 * d.Cq + 8.0 * d.m * kp + 64.0), make_int2(sys, r0)});
         }
         for (int c0 = 0; c0 < d.Cq; c0 += kColsB) {
@@ -1041,7 +1117,7 @@ int apc_batch_get_x(apc_batch *b, int32_t sys, int32_t worker, double *X_dev, in
     if (!b || !X_dev || sys < 0 || sys >= b->nsys || worker < 0 || worker >= b->m[sys] || ldx < b->k)
         return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
     const SysDesc &d = b->desc[sys];
-    x_out_kernel<<<256, 256, 0, static_cast<cudaStream_t>(stream)>>>(d.X, b->n[sys], d.npad, b->kp, b->k, worker,
+    x_out_kernel<<<256, 256, 0, static_cast<cudaStream_t>(stream)>>>(d.X, b->n[sys], d.npad, d.m, b->kp, b->k, worker,
                                                                      X_dev, ldx);
     BCK(b, cudaGetLastError());
     return APC_OK;
