@@ -303,6 +303,7 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     del As, Bs
+    torch.cuda.empty_cache()
     info = bt.info()
     bt.set_params([1.0] * nsys, [1.0] * nsys)  # in S for every system; the cost does not depend on them
     bt.reset()

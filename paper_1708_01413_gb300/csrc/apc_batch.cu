@@ -965,7 +965,10 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             bfail(b, APC_ERR_CUDA, "set-up of system %d failed", sys);
             return bail(APC_ERR_CUDA);
         }
-        // the single-system iteration buffers are not used by the batch
+        // the single-system iteration buffers and the FP64 copy of A (kept
+        // there for residuals) are not used by the batch
+        cudaFree(c->A);
+        c->A = nullptr;
         cudaFree(c->Q);
         c->Q = nullptr;
         cudaFree(c->xw);
