@@ -95,6 +95,24 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
  * Errors: INVALID_ARG unless 0 < mu_min <= mu_max <= 1. */
 int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho);
 
+/* apc_spectral_bounds -- estimates of mu_min and mu_max, the extreme
+ * eigenvalues of X = (1/m) sum_i Q_i Q_i^T (Eq. 3), from `steps` (1..4096)
+ * steps of the Lanczos process on X started from a pseudo-random vector
+ * (splitmix64 stream of `seed`).  Each step applies X once, as two passes of
+ * the iteration kernel over the stored bases (in the context's precision:
+ * BF16 bases give the eigenvalues of the BF16 X); the Lanczos vectors and the
+ * recurrence are FP64, and the extreme eigenvalues of the k x k tridiagonal
+ * matrix (the Ritz values) are found by bisection on the host.  Ritz values
+ * lie inside the spectrum and approach its ends from inside:
+ * mu_min <= *mu_min_host and *mu_max_host <= mu_max.  Theorem 1 needs an
+ * enclosing interval for a guaranteed rate: mu_max <= 1 always holds (X is a
+ * mean of orthogonal projectors), and the estimate of mu_min should be
+ * lowered by the caller's margin.  Uses the context's iteration state (a
+ * later apc_iterate needs apc_reset).  Errors: INVALID_ARG, NONFINITE,
+ * NOMEM, TIMEOUT, CUDA. */
+int apc_spectral_bounds(apc_ctx *ctx, int32_t steps, uint64_t seed, double *mu_min_host, double *mu_max_host,
+                        void *stream);
+
 /* apc_reset -- Algorithm 1 initialisation for right-hand side rhs_dev
  * (FP64, N, device; NULL = the b given to apc_setup): x_i(0) is the
  * least-norm solution A_i^T (A_i A_i^T)^{-1} b_i of block i and

@@ -26,6 +26,7 @@ ERRORS = {
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
     "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
+    "apc_spectral_bounds",
     "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
 )
@@ -74,6 +75,7 @@ def lib() -> C.CDLL:
                                    C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
     L.apc_backward.argtypes = [vp, vp, i64, dbl, dbl, vp, vp]
     L.apc_set_test_hooks.argtypes = [vp, i32, dbl]
+    L.apc_spectral_bounds.argtypes = [vp, i32, C.c_uint64, C.POINTER(dbl), C.POINTER(dbl), vp]
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_residual_noalloc.restype = C.c_int
     L.apc_last_error.argtypes = [vp]
@@ -185,6 +187,14 @@ class Context:
         _check(lib().apc_residual(self.handle, _ptr(x), _ptr(rhs), _ptr(resid_out), C.byref(rel),
                                   _stream(stream)), self.handle)
         return rel.value
+
+    def spectral_bounds(self, steps: int = 100, seed: int = 1, stream=None):
+        """Lanczos estimates (mu_min, mu_max) of the extreme eigenvalues of X
+        (Ritz values: inside the spectrum)."""
+        lo, hi = C.c_double(), C.c_double()
+        _check(lib().apc_spectral_bounds(self.handle, int(steps), C.c_uint64(seed), C.byref(lo), C.byref(hi),
+                                         _stream(stream)), self.handle)
+        return lo.value, hi.value
 
     def set_test_hooks(self, grid_barrier_skew: int = 0, timeout_s: float = 2.0):
         """Failure injection for tests (see apc_set_test_hooks in the header)."""
@@ -372,6 +382,7 @@ class Batch:
 def _device(dev):
     import torch
     return torch.cuda.device(dev)
+
 
 
 def _batch_rhs(B, n, k):

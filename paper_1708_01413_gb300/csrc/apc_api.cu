@@ -179,6 +179,10 @@ int residual(apc_ctx *c, const double *x, const double *rhs, double *out, double
 namespace apc {
 // Error text for entry points that have no context (read by apc_last_error(NULL)).
 void set_global_error_text(const char *msg) { g_setup_error = msg; }
+// `iters` passes of the iteration kernel in `mode` (used by apc_spectral.cu)
+int pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
+    return run_pass(c, mode, gamma, eta, iters, s);
+}
 }  // namespace apc
 
 extern "C" {
