@@ -87,6 +87,21 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
               const double *b_dev, const int64_t *row_offsets_host, int32_t m,
               const apc_options *opt, void *stream);
 
+/* apc_setup_rows -- apc_setup for a partition whose blocks are arbitrary
+ * (not necessarily contiguous) sets of rows (Sec. 2 only asks that the
+ * equations be split among the machines).  Block i holds rows
+ * row_index_host[row_offsets_host[i] .. row_offsets_host[i+1]-1] of [A, b],
+ * in that order; row_index_host (N int64, host) must list every row 0..N-1
+ * exactly once.  The rows are gathered once into the blocked order; the
+ * context keeps the permutation, so right-hand sides passed later
+ * (apc_reset, apc_residual) are given in the caller's row order and row-space
+ * results (apc_residual's residual vector, apc_backward's dL/db) come back in
+ * it.  Other arguments, limits and errors as apc_setup (INVALID_ARG also when
+ * row_index is not a permutation). */
+int apc_setup_rows(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t lda, const double *b_dev,
+                   const int64_t *row_index_host, const int64_t *row_offsets_host, int32_t m,
+                   const apc_options *opt, void *stream);
+
 /* apc_optimal_params -- Theorem 1: from mu_min, mu_max of
  * X = (1/m) sum_i A_i^T (A_i A_i^T)^{-1} A_i return the optimal rate
  * rho = (sqrt(kappa)-1)/(sqrt(kappa)+1) and (gamma*, eta*), the roots of

@@ -51,7 +51,7 @@ __all__ = [
     "relative_residual", "relative_error", "invariant_drift",
     "rate_apc", "rate_cimmino", "rate_consensus", "convergence_time",
     "apc_forward_linear", "apc_adjoint", "power_mu_max", "ApcTrace",
-    "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine",
+    "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine", "partition_rows",
 ]
 
 
@@ -67,6 +67,18 @@ def partition(A: np.ndarray, b: np.ndarray, row_offsets) -> list[tuple[np.ndarra
     if offs[0] != 0 or offs[-1] != A.shape[0] or any(offs[i + 1] <= offs[i] for i in range(len(offs) - 1)):
         raise ValueError("row_offsets must be strictly increasing from 0 to N")
     return [(A[offs[i]:offs[i + 1], :], b[offs[i]:offs[i + 1]]) for i in range(len(offs) - 1)]
+
+
+def partition_rows(A: np.ndarray, b: np.ndarray, row_sets) -> list[tuple[np.ndarray, np.ndarray]]:
+    """The machines' blocks for an arbitrary (not necessarily contiguous)
+    assignment of equations (Sec. 2 only asks that the m subsets of the N
+    equations be given to m machines): block i holds the rows listed in
+    ``row_sets[i]``, in that order.  The sets must cover every row exactly once."""
+    rows = [np.asarray(r, dtype=np.int64) for r in row_sets]
+    allr = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+    if allr.size != A.shape[0] or not np.array_equal(np.sort(allr), np.arange(A.shape[0])):
+        raise ValueError("row_sets must cover every row exactly once")
+    return [(A[r, :], b[r]) for r in rows]
 
 
 def block_qr(A_i: np.ndarray, rank_tol: float | None = None) -> tuple[np.ndarray, np.ndarray]:

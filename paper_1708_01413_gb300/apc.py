@@ -26,7 +26,7 @@ ERRORS = {
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
     "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
-    "apc_spectral_bounds",
+    "apc_spectral_bounds", "apc_setup_rows",
     "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
 )
@@ -63,6 +63,8 @@ def lib() -> C.CDLL:
     vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
     L.apc_setup.argtypes = [C.POINTER(vp), vp, i64, i64, i64, vp, C.POINTER(i64), i32,
                             C.POINTER(apc_options), vp]
+    L.apc_setup_rows.argtypes = [C.POINTER(vp), vp, i64, i64, i64, vp, C.POINTER(i64), C.POINTER(i64), i32,
+                                 C.POINTER(apc_options), vp]
     L.apc_optimal_params.argtypes = [dbl, dbl, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl)]
     L.apc_reset.argtypes = [vp, vp, vp]
     L.apc_iterate.argtypes = [vp, dbl, dbl, i64, vp]
@@ -278,6 +280,32 @@ def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:
     _check(lib().apc_residual_noalloc(_ptr(A), A.stride(0), A.shape[0], A.shape[1], _ptr(x), _ptr(rhs),
                                       _ptr(resid_out), C.byref(rel), _stream(stream)))
     return rel.value
+
+
+def apc_setup_rows(A, b, row_sets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,
+                   workers_per_warp=0) -> Context:
+    """Factor a partition whose blocks are arbitrary row sets: block i holds
+    the rows ``row_sets[i]`` of A (FP64 CUDA tensor, N x n) and b."""
+    import numpy as np
+    import torch
+    if not (A.is_cuda and b.is_cuda) or A.dtype != torch.float64 or b.dtype != torch.float64:
+        raise TypeError("A and b must be float64 CUDA tensors")
+    if A.dim() != 2 or A.stride(1) != 1:
+        raise ValueError("A must be a row-major 2-D tensor")
+    b = b.contiguous()
+    sets = [np.asarray(r, dtype=np.int64) for r in row_sets]
+    index = np.ascontiguousarray(np.concatenate(sets))
+    offs = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(r) for r in sets])]).astype(np.int64))
+    opt = apc_options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                      int(cluster_size), int(workers_per_warp), float(timeout_s))
+    h = C.c_void_p()
+    with torch.cuda.device(A.device):
+        rc = lib().apc_setup_rows(C.byref(h), _ptr(A), A.shape[0], A.shape[1], A.stride(0), _ptr(b),
+                                  index.ctypes.data_as(C.POINTER(C.c_int64)),
+                                  offs.ctypes.data_as(C.POINTER(C.c_int64)), len(sets), C.byref(opt),
+                                  _stream(stream))
+    _check(rc, None)
+    return Context(h, A.device, offs)
 
 
 def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,

@@ -54,7 +54,7 @@ int dalloc(apc_ctx *ctx, T **p, size_t bytes) {
 
 void free_all(apc_ctx *c) {
     void *ps[] = {c->d_rowstart, c->d_p, c->A, c->b, c->dinv, c->Rinv1, c->Rinv2, c->Q, c->xw, c->xbar,
-                  c->zbuf, c->bar, c->err, c->sums, c->xtmp, c->rtmp, c->xacc, c->rhs};
+                  c->zbuf, c->bar, c->err, c->sums, c->xtmp, c->rtmp, c->xacc, c->rhs, c->d_perm};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -176,6 +176,10 @@ int residual(apc_ctx *c, const double *x, const double *rhs, double *out, double
 
 }  // namespace
 
+namespace {
+int reset_blocked(apc_ctx *c, const double *rhs_dev, cudaStream_t s);
+}
+
 namespace apc {
 // Error text for entry points that have no context (read by apc_last_error(NULL)).
 void set_global_error_text(const char *msg) { g_setup_error = msg; }
@@ -186,6 +190,57 @@ int pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStre
 }  // namespace apc
 
 extern "C" {
+
+int apc_setup_rows(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t lda, const double *b_dev,
+                   const int64_t *row_index_host, const int64_t *row_offsets_host, int32_t m, const apc_options *opt,
+                   void *stream) {
+    if (!out) return fail(nullptr, APC_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!A_dev || !b_dev || !row_index_host || !row_offsets_host || N < 1 || n < 1 || lda < n)
+        return fail(nullptr, APC_ERR_INVALID_ARG, "apc_setup_rows: NULL argument or bad size");
+    // row_index must list every row exactly once
+    std::vector<char> seen(size_t(N), 0);
+    for (int64_t k = 0; k < N; ++k) {
+        const int64_t r = row_index_host[k];
+        if (r < 0 || r >= N || seen[size_t(r)])
+            return fail(nullptr, APC_ERR_INVALID_ARG, "apc_setup_rows: row_index is not a permutation of 0..N-1");
+        seen[size_t(r)] = 1;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int64_t *d_perm = nullptr;
+    double *Ag = nullptr, *bg = nullptr;
+    auto release = [&]() {
+        if (d_perm) cudaFree(d_perm);
+        if (Ag) cudaFree(Ag);
+        if (bg) cudaFree(bg);
+    };
+    if (cudaMalloc(&d_perm, sizeof(int64_t) * N) != cudaSuccess || cudaMalloc(&Ag, sizeof(double) * N * n) != cudaSuccess ||
+        cudaMalloc(&bg, sizeof(double) * N) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(nullptr, APC_ERR_NOMEM, "apc_setup_rows: cudaMalloc failed");
+    }
+    if (cudaMemcpyAsync(d_perm, row_index_host, sizeof(int64_t) * N, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        launch_gather_rows(A_dev, lda, N, n, d_perm, Ag, s) != cudaSuccess ||
+        launch_permute_vec(b_dev, d_perm, N, 0, bg, s) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(nullptr, APC_ERR_CUDA, "apc_setup_rows: gather failed");
+    }
+    // the blocked system's rows are contiguous: factor it as usual (its copy of A
+    // and b, in the blocked order, serves the residuals)
+    const int rc = apc_setup(out, Ag, N, n, n, bg, row_offsets_host, m, opt, stream);
+    cudaStreamSynchronize(s);
+    cudaFree(Ag);
+    cudaFree(bg);
+    Ag = bg = nullptr;
+    if (rc != APC_OK) {
+        release();
+        return rc;
+    }
+    (*out)->d_perm = d_perm;
+    return APC_OK;
+}
 
 int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho) {
     if (!(mu_min > 0.0) || !(mu_min <= mu_max) || !(mu_max <= 1.0 + 1e-12))
@@ -365,6 +420,18 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
 int apc_reset(apc_ctx *c, const double *rhs_dev, void *stream) {
     if (!c) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL context");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (rhs_dev && c->d_perm) {  // caller's row order -> the blocked order
+        CK(c, launch_permute_vec(rhs_dev, c->d_perm, c->N, 0, c->rtmp, s));
+        rhs_dev = c->rtmp;
+    }
+    return reset_blocked(c, rhs_dev, s);
+}
+
+}  // extern "C"
+
+namespace {
+// apc_reset with the right-hand side already in the blocked row order
+int reset_blocked(apc_ctx *c, const double *rhs_dev, cudaStream_t s) {
     const size_t ssz = s_elem_size(c->precision);
     const double *rhs = rhs_dev ? rhs_dev : c->b;
     CK(c, cudaMemsetAsync(c->zbuf, 0, ssz * 3 * c->m * c->P, s));
@@ -374,6 +441,9 @@ int apc_reset(apc_ctx *c, const double *rhs_dev, void *stream) {
     c->t = 0;
     return run_pass(c, MODE_INIT, 1.0, 1.0, 1, s);
 }
+}  // namespace
+
+extern "C" {
 
 int apc_iterate(apc_ctx *c, double gamma, double eta, int64_t iters, void *stream) {
     if (!c) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL context");
@@ -409,8 +479,16 @@ int apc_get_basis(apc_ctx *c, int32_t block, double *Q_dev, int64_t ldq, void *s
 int apc_residual(apc_ctx *c, const double *x_dev, const double *rhs_dev, double *resid_dev, double *rel_host,
                  void *stream) {
     if (!c || !x_dev || !rel_host) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
-    return residual(c, x_dev, rhs_dev ? rhs_dev : c->b, resid_dev ? resid_dev : c->rtmp, rel_host,
-                    static_cast<cudaStream_t>(stream));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!c->d_perm)
+        return residual(c, x_dev, rhs_dev ? rhs_dev : c->b, resid_dev ? resid_dev : c->rtmp, rel_host, s);
+    // rows were regrouped by apc_setup_rows: work in the blocked order, return
+    // the residual vector in the caller's order
+    if (rhs_dev) CK(c, launch_permute_vec(rhs_dev, c->d_perm, c->N, 0, c->rhs, s));
+    const int rc = residual(c, x_dev, rhs_dev ? c->rhs : c->b, c->rtmp, rel_host, s);
+    if (rc != APC_OK) return rc;
+    if (resid_dev) CK(c, launch_permute_vec(c->rtmp, c->d_perm, c->N, 1, resid_dev, s));
+    return APC_OK;
 }
 
 int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iters, int64_t check_every,
@@ -426,7 +504,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
     int rc = APC_OK;
     if (!refine) {
         sweeps = 1;
-        if ((rc = apc_reset(c, nullptr, s)) != APC_OK) return rc;
+        if ((rc = reset_blocked(c, nullptr, s)) != APC_OK) return rc;
         CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
         if ((rc = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return rc;
         const double rel0 = rel;
@@ -457,7 +535,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
         while (iters < max_iters && sweeps < max_sweeps) {
             if (rel <= tol) { rc = APC_OK; break; }
             ++sweeps;
-            int r2 = apc_reset(c, c->rhs, s);
+            int r2 = reset_blocked(c, c->rhs, s);
             if (r2 != APC_OK) return r2;
             double best = 1.0, prev = 1.0, inner = 1.0;
             // inner APC on A delta = r; stop when its residual stagnates
@@ -513,7 +591,8 @@ int apc_backward(apc_ctx *c, const double *g_dev, int64_t T, double gamma, doubl
     if ((rc = run_pass(c, MODE_ADJ_FINAL, gamma, eta, 1, s)) != APC_OK) return rc;
     const void *v = static_cast<const char *>(c->zbuf) + ssz * size_t(c->t % 3) * c->m * c->P;
     CK(c, launch_bsolve(v, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P, state_prec(c->precision),
-                        db_dev, s));
+                        c->d_perm ? c->rtmp : db_dev, s));
+    if (c->d_perm) CK(c, launch_permute_vec(c->rtmp, c->d_perm, c->N, 1, db_dev, s));  // caller's row order
     c->t = 0;  // the iteration state now holds the reverse sweep: apc_iterate needs apc_reset
     return APC_OK;
 }

@@ -28,6 +28,7 @@ struct apc_ctx {
     double timeout_s = 2.0;
     uint32_t test_barrier_skew = 0;
     size_t q_bytes = 0;
+    int64_t *d_perm = nullptr;  // apc_setup_rows: row k of the blocked system is row d_perm[k] of the caller's
     std::string last_error;
 };
 

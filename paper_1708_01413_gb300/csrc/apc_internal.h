@@ -101,6 +101,11 @@ cudaError_t launch_unpack_x(const void *xw, int precision, int64_t n, int m, dou
 cudaError_t launch_get_basis(const void *Q, int precision, int64_t n, int m, int P, int b, int p, double *out,
                              int64_t ldq, cudaStream_t s);
 cudaError_t launch_axpy_f64(double *y, const double *x, double a, int64_t count, cudaStream_t s);
+cudaError_t launch_gather_rows(const double *A, int64_t lda, int64_t N, int64_t n, const int64_t *perm,
+                               double *out, cudaStream_t s);
+// gather (scatter = 0): out[k] = v[perm[k]];  scatter (1): out[perm[k]] = v[k]
+cudaError_t launch_permute_vec(const double *v, const int64_t *perm, int64_t N, int scatter, double *out,
+                               cudaStream_t s);
 // flags[0] |= 1 if any of v[0..count) is not finite.
 cudaError_t launch_check_finite(const double *v, int64_t count, int *flag, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 // The second pass restores orthogonality lost in the first.  GB300 has few
 // FP64 units, so these kernels are plain register-tiled FP64 FMA loops; their
 // cost is paid once per system.
+#include <algorithm>
 #include <cstdio>
 #include "apc_internal.h"
 
@@ -374,6 +375,27 @@ __global__ void axpy_kernel(double *y, const double *x, double a, int64_t count)
         y[i] = fma(a, x[i], y[i]);
 }
 
+// out[k][:] = A[perm[k]][:]  (rows of an N x n row-major matrix)
+__global__ void gather_rows_kernel(const double *A, int64_t lda, int64_t N, int64_t n, const int64_t *perm,
+                                   double *out) {
+    const int64_t total = N * n;
+    for (int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t k = idx / n, j = idx - k * n;
+        out[idx] = A[perm[k] * lda + j];
+    }
+}
+
+// out[k] = v[perm[k]] (gather) or out[perm[k]] = v[k] (scatter)
+__global__ void permute_vec_kernel(const double *v, const int64_t *perm, int64_t N, int scatter, double *out) {
+    for (int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; k < N; k += int64_t(gridDim.x) * blockDim.x) {
+        if (scatter)
+            out[perm[k]] = v[k];
+        else
+            out[k] = v[perm[k]];
+    }
+}
+
 __global__ void finite_kernel(const double *v, int64_t count, int *flag) {
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
         if (!isfinite(v[i])) atomicOr(flag, 1);
@@ -385,6 +407,20 @@ inline unsigned grid1d(int64_t count, int threads) {
 }
 
 }  // namespace
+
+cudaError_t launch_gather_rows(const double *A, int64_t lda, int64_t N, int64_t n, const int64_t *perm,
+                               double *out, cudaStream_t s) {
+    const unsigned g = unsigned(std::min<int64_t>((N * n + 255) / 256, 152 * 64));
+    gather_rows_kernel<<<g, 256, 0, s>>>(A, lda, N, n, perm, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_vec(const double *v, const int64_t *perm, int64_t N, int scatter, double *out,
+                               cudaStream_t s) {
+    const unsigned g = unsigned(std::min<int64_t>((N + 255) / 256, 152 * 16));
+    permute_vec_kernel<<<g, 256, 0, s>>>(v, perm, N, scatter, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rownorm(const double *A, int64_t lda, int64_t N, int64_t n, double *dinv, int *err,
                            cudaStream_t s) {

@@ -91,3 +91,31 @@ def test_power_mu_max_matches_eigvalsh():
     lo, hi = O.mu_bounds(Qs)
     est = O.power_mu_max(Qs, np.random.default_rng(1).standard_normal(40), 400)
     assert est == pytest.approx(hi, rel=1e-6)
+
+
+def test_partition_rows_arbitrary_sets():
+    # Sec. 2: any assignment of the equations to machines; the APC limit is the
+    # same solution (the method never uses the row order), and each block's
+    # projector depends only on its set of rows
+    import numpy as np
+    from oracle import apc_oracle as O
+    from paper_1708_01413_gb300 import inputs
+    A, x_true, b = inputs.gaussian_system(60, 41)
+    sets = [np.arange(i, 60, 4) for i in range(4)]  # round-robin, 15 rows each
+    blocks = O.partition_rows(A, b, sets)
+    for (Ai, bi), r in zip(blocks, sets):
+        assert np.array_equal(Ai, A[r]) and np.array_equal(bi, b[r])
+    # permuting the rows inside a set leaves the projector unchanged
+    P1 = O.projector(blocks[0][0])
+    P2 = O.projector(A[sets[0][::-1]])
+    assert np.allclose(P1, P2, atol=1e-12)
+    Qs = [O.block_qr(Ai)[0] for Ai, _ in blocks]
+    g, e, _ = O.optimal_params(*O.mu_bounds(Qs))
+    # gather the rows block by block and run on the contiguous system
+    order = np.concatenate(sets)
+    offs = np.concatenate([[0], np.cumsum([len(r) for r in sets])])
+    tr = O.apc_run(A[order], b[order], offs, g, e, max_iters=20000, tol=1e-12)
+    assert tr.converged
+    assert np.linalg.norm(tr.xbar - x_true) <= 1e-9 * np.linalg.norm(x_true)
+    with pytest.raises(ValueError):
+        O.partition_rows(A, b, [np.arange(0, 30), np.arange(29, 60)])
