@@ -52,6 +52,7 @@ __all__ = [
     "rate_apc", "rate_cimmino", "rate_consensus", "convergence_time",
     "apc_forward_linear", "apc_adjoint", "power_mu_max", "ApcTrace",
     "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine", "partition_rows",
+    "precondition_blocks", "hb_optimal_params", "dhbm_step", "dhbm_run",
 ]
 
 
@@ -436,3 +437,52 @@ def apc_run_affine(Qs, cs, gamma: float, eta: float, T: int):
     for _ in range(T):
         xs, xbar = apc_step_affine(xs, xbar, Qs, cs, gamma, eta)
     return xs, xbar
+
+
+# ---------------------------------------------------------------------------
+# Distributed heavy-ball method with the distributed preconditioning of Sec. 6
+# ---------------------------------------------------------------------------
+
+def precondition_blocks(blocks):
+    """Sec. 6: machine i premultiplies [A_i, b_i] by (A_i A_i^T)^{-1/2}, giving
+    [C_i, d_i].  The inverse square root is formed from the eigendecomposition
+    of the symmetric positive definite A_i A_i^T (no QR involved)."""
+    out = []
+    for A_i, b_i in blocks:
+        lam, V = np.linalg.eigh(A_i @ A_i.T)
+        if lam.min() <= 0:
+            raise np.linalg.LinAlgError("A_i A_i^T is singular")
+        S = (V / np.sqrt(lam)) @ V.T
+        out.append((S @ A_i, S @ b_i))
+    return out
+
+
+def hb_optimal_params(L_min: float, L_max: float) -> tuple[float, float, float]:
+    """Step size alpha and momentum beta of the heavy-ball method (the D-HBM
+    update of Sec. 4.3) for a quadratic whose Hessian has spectrum in [L_min, L_max]:
+    alpha = 4 / (sqrt(L_max) + sqrt(L_min))^2,
+    beta = ((sqrt(L_max) - sqrt(L_min)) / (sqrt(L_max) + sqrt(L_min)))^2, which
+    attain the rate (sqrt(kappa) - 1) / (sqrt(kappa) + 1) that Sec. 4.3 quotes
+    (Polyak's choice; the paper states only the rate).  Returns (alpha, beta, rho)."""
+    if not (0.0 < L_min <= L_max):
+        raise ValueError("need 0 < L_min <= L_max")
+    a, c = math.sqrt(L_max), math.sqrt(L_min)
+    return 4.0 / (a + c) ** 2, ((a - c) / (a + c)) ** 2, (a - c) / (a + c)
+
+
+def dhbm_step(pblocks, x: np.ndarray, z: np.ndarray, alpha: float, beta: float):
+    """One D-HBM iteration (Sec. 4.3) on the blocks [C_i, d_i]:
+        z(t+1) = beta z(t) + sum_i C_i^T (C_i x(t) - d_i),
+        x(t+1) = x(t) - alpha z(t+1)."""
+    g = sum(C_i.T @ (C_i @ x - d_i) for C_i, d_i in pblocks)
+    z = beta * z + g
+    return x - alpha * z, z
+
+
+def dhbm_run(pblocks, x0: np.ndarray, alpha: float, beta: float, T: int):
+    """T iterations of ``dhbm_step`` from x0 with z(0) = 0; returns x(T)."""
+    x = np.array(x0, dtype=np.float64, copy=True)
+    z = np.zeros_like(x)
+    for _ in range(T):
+        x, z = dhbm_step(pblocks, x, z, alpha, beta)
+    return x
