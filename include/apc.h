@@ -128,6 +128,16 @@ int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta,
 int apc_spectral_bounds(apc_ctx *ctx, int32_t steps, uint64_t seed, double *mu_min_host, double *mu_max_host,
                         void *stream);
 
+/* apc_hb_optimal_params -- step size and momentum of the heavy-ball method
+ * on the system preconditioned as in Sec. 6 (each block premultiplied by
+ * (A_i A_i^T)^{-1/2}, so that C^T C = m X): with the spectrum of m X in
+ * [m mu_min, m mu_max], alpha = 4 / (sqrt(m mu_max) + sqrt(m mu_min))^2,
+ * beta = rho^2, rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1), the rate Sec. 4.3
+ * quotes for D-HBM and Sec. 6 for its preconditioned form (the same as APC's).
+ * Pure host arithmetic.  Errors: INVALID_ARG unless 0 < mu_min <= mu_max <= 1
+ * and m >= 1. */
+int apc_hb_optimal_params(double mu_min, double mu_max, int32_t m, double *alpha, double *beta, double *rho);
+
 /* apc_reset -- Algorithm 1 initialisation for right-hand side rhs_dev
  * (FP64, N, device; NULL = the b given to apc_setup): x_i(0) is the
  * least-norm solution A_i^T (A_i A_i^T)^{-1} b_i of block i and

@@ -63,7 +63,21 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
  * finite (nothing is changed then), INVALID_ARG, CUDA. */
 int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *eta_host);
 
-/* apc_batch_reset -- Algorithm 1 initialisation of every system.  With
+/* apc_batch_set_hb_params -- switch later apc_batch_iterate calls to the
+ * distributed heavy-ball method on the preconditioned system of Sec. 6
+ * (C_i = (A_i A_i^T)^{-1/2} A_i, d_i = (A_i A_i^T)^{-1/2} b_i; any orthonormal
+ * basis of the row space gives the same gradient, so the stored Q_i and c_i
+ * serve): per system
+ *     zeta <- beta zeta + sum_i Q_i (Q_i^T x - c_i),   x <- x - alpha zeta
+ * (the D-HBM update of Sec. 4.3), with x the master's estimate
+ * (apc_batch_get_xbar) and zeta = 0 after apc_batch_reset.  alpha_host and
+ * beta_host hold one value per system (see apc_hb_optimal_params).
+ * apc_batch_set_params switches back to APC.  Errors: PARAMS unless
+ * alpha > 0 and 0 <= beta < 1 (nothing is changed then), INVALID_ARG, CUDA. */
+int apc_batch_set_hb_params(apc_batch *b, const double *alpha_host, const double *beta_host);
+
+/* apc_batch_reset -- Algorithm 1 initialisation of every system (and a zero
+ * heavy-ball momentum).  With
  * B_dev_host non-NULL the right-hand sides are replaced first (same layout
  * as in apc_batch_setup).  Errors: INVALID_ARG, TIMEOUT, CUDA. */
 int apc_batch_reset(apc_batch *b, const double *const *B_dev_host, void *stream);

@@ -26,7 +26,7 @@ ERRORS = {
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
     "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
-    "apc_spectral_bounds", "apc_setup_rows",
+    "apc_spectral_bounds", "apc_setup_rows", "apc_hb_optimal_params", "apc_batch_set_hb_params",
     "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
 )
@@ -87,6 +87,8 @@ def lib() -> C.CDLL:
     L.apc_batch_setup.argtypes = [C.POINTER(vp), i32, C.POINTER(i64), C.POINTER(i32), C.POINTER(i64),
                                   C.POINTER(vp), C.POINTER(vp), i32, C.POINTER(apc_options), vp]
     L.apc_batch_set_params.argtypes = [vp, C.POINTER(dbl), C.POINTER(dbl)]
+    L.apc_batch_set_hb_params.argtypes = [vp, C.POINTER(dbl), C.POINTER(dbl)]
+    L.apc_hb_optimal_params.argtypes = [dbl, dbl, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(dbl)]
     L.apc_batch_reset.argtypes = [vp, vp, vp]
     L.apc_batch_iterate.argtypes = [vp, i64, vp]
     L.apc_batch_get_xbar.argtypes = [vp, i32, vp, i64, vp]
@@ -119,6 +121,13 @@ def _check(rc: int, ctx=None):
     if rc != 0:
         msg = lib().apc_last_error(ctx).decode(errors="replace")
         raise ApcError(rc, msg)
+
+
+def apc_hb_optimal_params(mu_min: float, mu_max: float, m: int):
+    """(alpha, beta, rho) of heavy ball on the Sec. 6 preconditioned system."""
+    a, b, r = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().apc_hb_optimal_params(mu_min, mu_max, int(m), C.byref(a), C.byref(b), C.byref(r)))
+    return a.value, b.value, r.value
 
 
 def apc_optimal_params(mu_min: float, mu_max: float):
@@ -373,6 +382,16 @@ class Batch:
             raise ValueError("one gamma and one eta per system")
         _check_batch(lib().apc_batch_set_params(self.handle, g.ctypes.data_as(C.POINTER(C.c_double)),
                                                 e.ctypes.data_as(C.POINTER(C.c_double))), self.handle)
+
+    def set_hb_params(self, alphas, betas):
+        """Switch to the preconditioned heavy-ball method (Sec. 4.3 / Sec. 6)."""
+        import numpy as np
+        a = np.ascontiguousarray(np.asarray(alphas, dtype=np.float64))
+        b_ = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        if a.shape != (len(self.n),) or b_.shape != (len(self.n),):
+            raise ValueError("one alpha and one beta per system")
+        _check_batch(lib().apc_batch_set_hb_params(self.handle, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                                   b_.ctypes.data_as(C.POINTER(C.c_double))), self.handle)
 
     def reset(self, B=None, stream=None):
         arr = None

@@ -242,6 +242,17 @@ int apc_setup_rows(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int
     return APC_OK;
 }
 
+int apc_hb_optimal_params(double mu_min, double mu_max, int32_t m, double *alpha, double *beta, double *rho) {
+    if (!(mu_min > 0.0) || !(mu_min <= mu_max) || !(mu_max <= 1.0 + 1e-12) || m < 1 || !alpha || !beta || !rho)
+        return fail(nullptr, APC_ERR_INVALID_ARG, "need 0 < mu_min <= mu_max <= 1, m >= 1 and non-NULL outputs");
+    // Hessian of the preconditioned least squares: C^T C = m X, spectrum [m mu_min, m mu_max]
+    const double a = std::sqrt(m * mu_max), c = std::sqrt(m * mu_min);
+    *alpha = 4.0 / ((a + c) * (a + c));
+    *rho = (a - c) / (a + c);
+    *beta = (*rho) * (*rho);
+    return APC_OK;
+}
+
 int apc_optimal_params(double mu_min, double mu_max, double *gamma, double *eta, double *rho) {
     if (!(mu_min > 0.0) || !(mu_min <= mu_max) || !(mu_max <= 1.0 + 1e-12))
         return fail(nullptr, APC_ERR_INVALID_ARG, "need 0 < mu_min <= mu_max <= 1 (got %g, %g)", mu_min, mu_max);

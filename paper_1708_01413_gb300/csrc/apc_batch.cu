@@ -89,8 +89,10 @@ struct SysDesc {
     uint2 *Zfrag;            // [Cq/8][MT][kPlanesA][32]     z operand planes
     const float4 *Cfrag;     // [Cq/8][MT][32]               c_i, FP32
     const int *coloff;       // [m + 1], multiples of 16
+    float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float
     int npad, m, Cq, C;
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo, im_hi, im_lo;
+    float na_hi, na_lo, hb_hi, hb_lo;  // heavy ball: -alpha and beta
 };
 
 struct BatchArgs {
@@ -101,6 +103,7 @@ struct BatchArgs {
     const int *offB;     // [grid + 1]
     int64_t iters;
     int init;
+    int hb;              // 1: distributed-preconditioned heavy ball instead of APC
     uint32_t barrier_skew;
     uint32_t *bar;
     int *err;
@@ -246,7 +249,7 @@ __device__ __forceinline__ bool acquire_slot(const Ring &R, uint64_t *empty, int
 
 // ---- sweep A ---------------------------------------------------------------------
 template <int MT>
-__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init,
+__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool no_x,
                                  uint64_t policy) {
     constexpr int KP = 16 * MT;
     const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
@@ -257,7 +260,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory ring
     constexpr int kPrefetch = 4;
     for (int w = 0; w < min(kPrefetch, nwin); ++w) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w), qbytes);
-    if (!init)
+    if (!no_x)
         for (int j = 0; j < min(kPrefetch, d.m); ++j) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, j), xbytes);
     for (int w = 0; w < nwin; ++w) {
         const uint32_t s = cur.q % kQSlots;
@@ -269,7 +272,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
         if (w + kPrefetch < nwin) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w + kPrefetch), qbytes);
         ++cur.q;
         // x_i tiles of the machines whose last chunk lies in this window
-        while (!init && pi < d.m && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
+        while (!no_x && pi < d.m && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
             const uint32_t xs = cur.x % kXSlots;
             if (!acquire_slot(R, R.xempty, kXSlots, cur.x)) return;
             mbar_arrive_expect_tx(&R.xfull[xs], xbytes);
@@ -282,8 +285,8 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
 }
 
 template <int MT>
-__device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init, float gh,
-                                 float gl) {
+__device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init, bool hb,
+                                 float gh, float gl) {
     constexpr int KP = 16 * MT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
     const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
@@ -305,7 +308,7 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, i
                 xbh[mt][nt][e] = 0.0f;
                 xbl[mt][nt][e] = 0.0f;
             }
-    if (wact && !init) {
+    if (wact && !init && !hb) {
 #pragma unroll
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
@@ -356,7 +359,11 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, i
 #pragma unroll
                         for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
             }
-            if (c16 + 1 == iend) {
+            if (c16 + 1 == iend && hb) {
+                // heavy ball: the accumulator keeps summing over the machines
+                ++i;
+                if (i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
+            } else if (c16 + 1 == iend) {
                 // machine i is complete: x_i <- x_i + gamma (xbar - x_i - w_i), row sums
                 uint32_t xs = 0, sx = 0;
                 if (!init) {
@@ -403,28 +410,57 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, i
         ++cur.q;
     }
     if (!wact) return;
-    // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
-    const float2 em = make_float2(init ? d.im_hi : d.em_hi, init ? d.im_lo : d.em_lo);
-    const float2 e1 = make_float2(d.e1_hi, d.e1_lo);
     float xo[MT][4][4];
+    if (hb) {
+        // heavy ball on the preconditioned system (Sec. 4.3 update, Sec. 6):
+        // the accumulator holds the gradient sum_i Q_i (Q_i^T x - c_i);
+        // zeta <- beta zeta + gradient, x <- x - alpha zeta
+        const float2 beta = make_float2(d.hb_hi, d.hb_lo), nalpha = make_float2(d.na_hi, d.na_lo);
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
+        for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
+            for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                float2 xn[2];
+                for (int h = 0; h < 2; ++h) {
+                    const int rhs = 16 * mt + g + 8 * h;
+                    const size_t off = size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq;
+                    const float4 xv = __ldcg(reinterpret_cast<const float4 *>(d.Xb + off));
+                    const float4 mv = __ldcg(reinterpret_cast<const float4 *>(d.Mb + off));
+                    const float2 x2[2] = {make_float2(xv.x, xv.y), make_float2(xv.z, xv.w)};
+                    const float2 m2[2] = {make_float2(mv.x, mv.y), make_float2(mv.z, mv.w)};
+                    float2 xn[2], zn[2];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int e = 2 * h + u;
-                    xn[u] = dfm(em, make_float2(S[mt][nt][e], 0.0f));
-                    if (!init) xn[u] = dfa(xn[u], dfm(e1, make_float2(xbh[mt][nt][e], xbl[mt][nt][e])));
-                    xo[mt][nt][e] = xn[u].x;
+                    for (int u = 0; u < 2; ++u) {
+                        zn[u] = dfa(dfm(beta, m2[u]), make_float2(acc[mt][nt][2 * h + u], 0.0f));
+                        xn[u] = dfa(x2[u], dfm(nalpha, zn[u]));
+                        xo[mt][nt][2 * h + u] = xn[u].x;
+                    }
+                    __stcg(reinterpret_cast<float4 *>(d.Mb + off), make_float4(zn[0].x, zn[0].y, zn[1].x, zn[1].y));
+                    __stcg(reinterpret_cast<float4 *>(d.Xb + off), make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
                 }
-                const int rhs = 16 * mt + g + 8 * h;
-                __stcg(reinterpret_cast<float4 *>(d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq),
-                       make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
-            }
+    } else {
+        // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
+        const float2 em = make_float2(init ? d.im_hi : d.em_hi, init ? d.im_lo : d.em_lo);
+        const float2 e1 = make_float2(d.e1_hi, d.e1_lo);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float2 xn[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int e = 2 * h + u;
+                        xn[u] = dfm(em, make_float2(S[mt][nt][e], 0.0f));
+                        if (!init) xn[u] = dfa(xn[u], dfm(e1, make_float2(xbh[mt][nt][e], xbl[mt][nt][e])));
+                        xo[mt][nt][e] = xn[u].x;
+                    }
+                    const int rhs = 16 * mt + g + 8 * h;
+                    __stcg(reinterpret_cast<float4 *>(d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq),
+                           make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
+                }
+    }
     // xbar' operand planes of sweep B: in the 16-row chunk kc of this warp,
     // a0/a1 are n-tile 2kc (rhs g / g+8) and a2/a3 n-tile 2kc+1
 #pragma unroll
@@ -600,10 +636,11 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
         for (int u = a.offA[blockIdx.x]; u < a.offA[blockIdx.x + 1] && !R.aborted(); ++u) {
             const int2 U = a.unitsA[u];
             const SysDesc &d = a.sys[U.x];
+            const bool hb = a.hb && !init;
             if (producer) {
-                if (lane == 0) sweep_a_producer<MT>(R, cur, d, U.y, init, policy);
+                if (lane == 0) sweep_a_producer<MT>(R, cur, d, U.y, init || hb, policy);
             } else {
-                sweep_a_consumer<MT>(R, cur, d, U.y, init, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
+                sweep_a_consumer<MT>(R, cur, d, U.y, init, hb, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
             }
         }
         ++episode;
@@ -731,11 +768,13 @@ struct apc_batch {
     uint32_t *bar = nullptr;
     int *err = nullptr;
     bool reset_done = false, params_set = false;
+    int method = 0;  // 0: APC, 1: heavy ball (apc_batch_set_hb_params)
     int64_t q_bytes = 0, state_bytes = 0;
     double timeout_s = 2.0;
     uint32_t barrier_skew = 0;
     cudaGraphExec_t graph = nullptr;
     int64_t graph_iters = -1;
+    int graph_method = -1;
     std::string last_error;
 };
 
@@ -806,6 +845,7 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
     a.offB = b->d_offB;
     a.iters = iters;
     a.init = init;
+    a.hb = init ? 0 : b->method;
     a.barrier_skew = b->barrier_skew;
     a.bar = b->bar;
     a.err = b->err;
@@ -938,6 +978,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             (rc = balloc(b, &d.Xfrag, sizeof(uint4) * size_t(npad / 16) * MT * kPlanesB * 32)) ||
             (rc = balloc(b, &d.Zfrag, sizeof(uint2) * size_t(Cq / 8) * MT * kPlanesA * 32)) ||
             (rc = balloc(b, &Cf, sizeof(float4) * size_t(Cq / 8) * MT * 32)) ||
+            (rc = balloc(b, &d.Mb, sizeof(float2) * size_t(kp) * npad)) ||
             (rc = balloc(b, &Bc, sizeof(double) * size_t(n) * k)))
             return bail(rc);
         d.Q = Q;
@@ -951,6 +992,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         cudaMemcpyAsync(Bc, B_dev_host[sys], sizeof(double) * n * k, cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(d.X, 0, sizeof(float) * x_elems, s);
         cudaMemsetAsync(d.Xb, 0, sizeof(float2) * size_t(kp) * npad, s);
+        cudaMemsetAsync(d.Mb, 0, sizeof(float2) * size_t(kp) * npad, s);
         const unsigned grid = unsigned(std::min<int64_t>((npad * Cq + 255) / 256, 152 * 32));
         repack_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->Q), n, m, c->P, d_cb, d_co, c->d_p,
                                            int(npad), Cq, Q);
@@ -1051,6 +1093,26 @@ int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *e
     }
     BCK(b, cudaMemcpy(b->d_desc, b->desc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice));
     b->params_set = true;
+    b->method = 0;
+    return APC_OK;
+}
+
+int apc_batch_set_hb_params(apc_batch *b, const double *alpha_host, const double *beta_host) {
+    if (!b || !alpha_host || !beta_host) return bfail(b, APC_ERR_INVALID_ARG, "NULL argument");
+    for (int sys = 0; sys < b->nsys; ++sys) {
+        const double a = alpha_host[sys], be = beta_host[sys];
+        if (!(a > 0.0) || !std::isfinite(a) || !(be >= 0.0 && be < 1.0))
+            return bfail(b, APC_ERR_PARAMS, "system %d: need alpha > 0 and 0 <= beta < 1 (alpha=%g, beta=%g)", sys, a,
+                         be);
+    }
+    for (int sys = 0; sys < b->nsys; ++sys) {
+        SysDesc &d = b->desc[sys];
+        split_f64(-alpha_host[sys], d.na_hi, d.na_lo);
+        split_f64(beta_host[sys], d.hb_hi, d.hb_lo);
+    }
+    BCK(b, cudaMemcpy(b->d_desc, b->desc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice));
+    b->params_set = true;
+    b->method = 1;
     return APC_OK;
 }
 
@@ -1067,6 +1129,8 @@ int apc_batch_reset(apc_batch *b, const double *const *B_dev_host, void *stream)
             if (rc != APC_OK) return rc;
         }
     }
+    for (int sys = 0; sys < b->nsys; ++sys)
+        BCK(b, cudaMemsetAsync(b->desc[sys].Mb, 0, sizeof(float2) * size_t(b->kp) * b->desc[sys].npad, s));
     int rc = launch(b, 1, 1, s);
     if (rc != APC_OK) return rc;
     if ((rc = check_err(b, s)) != APC_OK) return rc;
@@ -1083,7 +1147,7 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // one persistent launch (barrier reset + kernel), captured once per
     // iteration count and replayed as a CUDA graph
-    if (!b->graph || b->graph_iters != iters) {
+    if (!b->graph || b->graph_iters != iters || b->graph_method != b->method) {
         if (b->graph) {
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;
@@ -1103,6 +1167,7 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
             return bfail(b, APC_ERR_CUDA, "graph capture of the batched launch failed");
         }
         b->graph_iters = iters;
+        b->graph_method = b->method;
     }
     BCK(b, cudaGraphLaunch(b->graph, s));
     return check_err(b, s);

@@ -228,3 +228,62 @@ def test_batch_full_workload_sampled_parity():
         Qs, Rs, cs = _oracle_system(A, B, offs[s])
         _, ref = O.apc_run_affine([O.round_bf16(Q) for Q in Qs], cs, 1.0, 1.0, T)
         assert _rel(bt.xbar(s).cpu().numpy(), ref) <= TOL, s
+
+
+@pytest.mark.parametrize("k", [5, 20])
+def test_batch_heavy_ball_matches_oracle_dhbm(k):
+    # Sec. 6 preconditioned D-HBM: gradient sum_i Q_i (Q_i^T x - c_i) on the
+    # BF16 bases, started from xbar(0) with zero momentum
+    apc, dev = _apc(), _dev()
+    systems = _systems([90, 300], k, seed=40 + k)
+    T = 20
+    refs, params = [], []
+    for A, B, offs in systems:
+        Qs, Rs, cs = _oracle_system(A, B, offs)
+        lo, hi = O.mu_bounds(Qs)
+        alpha, beta, _ = O.hb_optimal_params(len(Qs) * lo, len(Qs) * hi)
+        params.append((alpha, beta))
+        Qr = [O.round_bf16(Q) for Q in Qs]
+        x0 = sum(Q @ c for Q, c in zip(Qr, cs)) / len(Qr)
+        refs.append(O.dhbm_run([(Q.T, c) for Q, c in zip(Qr, cs)], x0, alpha, beta, T))
+    bt = apc.apc_batch_setup([torch.tensor(A, device=dev) for A, _, _ in systems],
+                             [torch.tensor(B, device=dev) for _, B, _ in systems],
+                             [offs for _, _, offs in systems])
+    bt.set_hb_params([p[0] for p in params], [p[1] for p in params])
+    bt.reset()
+    bt.iterate(T)
+    for s, ref in enumerate(refs):
+        assert _rel(bt.xbar(s).cpu().numpy(), ref) <= TOL, s
+    # back to APC: the same batch reproduces the APC trajectory
+    refs_apc = []
+    for (A, B, offs) in systems:
+        Qs, Rs, cs = _oracle_system(A, B, offs)
+        g, e, _ = O.optimal_params(*O.mu_bounds(Qs))
+        refs_apc.append((g, e, O.apc_run_affine([O.round_bf16(Q) for Q in Qs], cs, g, e, T)[1]))
+    bt.set_params([r[0] for r in refs_apc], [r[1] for r in refs_apc])
+    bt.reset()
+    bt.iterate(T)
+    for s, (_, _, ref) in enumerate(refs_apc):
+        assert _rel(bt.xbar(s).cpu().numpy(), ref) <= TOL, s
+
+
+def test_batch_heavy_ball_reaches_the_bf16_fixed_point():
+    # heavy ball on C x = d with C_i = Q_i^T, d_i = c_i solves the normal
+    # equations (sum_i Q_i Q_i^T) x = sum_i Q_i c_i: the same limit as APC
+    apc, dev = _apc(), _dev()
+    rng = np.random.default_rng(22)
+    n, k = 96, 3
+    A = rng.standard_normal((n, n)) + 2.0 * np.sqrt(n) * np.eye(n)
+    B = rng.standard_normal((n, k))
+    offs = inputs.uneven_offsets(n, 16, 40, rng)
+    Qs, Rs, cs = _oracle_system(A, B, offs)
+    Qr = [O.round_bf16(Q) for Q in Qs]
+    x_fp = np.linalg.solve(sum(Q @ Q.T for Q in Qr), sum(Q @ c for Q, c in zip(Qr, cs)))
+    lo, hi = O.mu_bounds(Qs)
+    alpha, beta, rho = apc.apc_hb_optimal_params(lo, hi, len(Qs))
+    T = int(np.ceil(np.log(1e-9) / np.log(rho))) + 100
+    bt = apc.apc_batch_setup([torch.tensor(A, device=dev)], [torch.tensor(B, device=dev)], [offs])
+    bt.set_hb_params([alpha], [beta])
+    bt.reset()
+    bt.iterate(T)
+    assert _rel(bt.xbar(0).cpu().numpy(), x_fp) <= 1e-5

@@ -51,3 +51,18 @@ def test_product_path_has_no_oracle_import():
             if f.endswith(".py"):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from\s+oracle|import\s+oracle)", text, flags=re.M), f
+
+
+def test_hb_optimal_params_host_entry_matches_oracle():
+    # pure host arithmetic: Sec. 6 preconditioning makes the Hessian m X
+    from oracle import apc_oracle as O
+    from paper_1708_01413_gb300 import apc
+    for lo, hi, m in ((1e-4, 0.9, 8), (0.3, 0.31, 3), (5e-8, 1.0, 128)):
+        a, b, r = apc.apc_hb_optimal_params(lo, hi, m)
+        a0, b0, r0 = O.hb_optimal_params(m * lo, m * hi)
+        assert a == pytest.approx(a0, rel=1e-12) and b == pytest.approx(b0, rel=1e-12)
+        assert r == pytest.approx(r0, rel=1e-12)
+        assert r == pytest.approx(O.optimal_params(lo, hi)[2], rel=1e-9)  # the APC rate
+    with pytest.raises(apc.ApcError) as ei:
+        apc.apc_hb_optimal_params(0.5, 0.2, 4)
+    assert ei.value.name == "INVALID_ARG"
