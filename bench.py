@@ -21,7 +21,9 @@ Also on the same JSON line:
   batch        the batched solver on 256 independent systems (n ~ U{256..4096},
                A = G + 0.5 sqrt(n) I, blocks p_i ~ U{16..128}, k = 32
                right-hand sides, BF16 bases): iterations per second of the
-               whole batch and its roofline (HBM bytes and tensor-pipe work);
+               whole batch and its roofline (HBM bytes and tensor-pipe work),
+               and the preconditioned heavy-ball method (Sec. 6) on the same
+               kernel;
   cpu_baseline the FP64 oracle timed on a bounded sample (8 of the 128 blocks).
 
 `--impl reference` times the FP64 CPU oracle alone on the same workload (the
@@ -317,6 +319,19 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
             b_.record(stream)
         torch.cuda.synchronize()
     sec = statistics.mean(a.elapsed_time(b_) for a, b_ in ev) / 1e3 / iters
+    # the preconditioned heavy-ball method (Sec. 6) on the same kernel: no
+    # machines' iterates, so its bytes per iteration are the two reads of Q
+    bt.set_hb_params([0.5] * nsys, [0.5] * nsys)
+    bt.reset()
+    bt.iterate(iters)
+    torch.cuda.synchronize()
+    hb0, hb1 = _ev(), _ev()
+    hb0.record(stream)
+    for _ in range(reps):
+        bt.iterate(iters)
+    hb1.record(stream)
+    torch.cuda.synchronize()
+    sec_hb = hb0.elapsed_time(hb1) / 1e3 / (reps * iters)
     alg = 2 * info["q_bytes"] + 2 * info["state_bytes"]
     ns = np.array([n for n, _ in specs], dtype=np.float64)
     kp = 16 if k <= 16 else 32
@@ -331,7 +346,11 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
             "clocks": clk.summary(),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "algorithmic_bytes_per_iter": alg, "kernel": "apc_batch_kernel",
-                         "tensor_tflops": mma_flops / sec / 1e12}}
+                         "tensor_tflops": mma_flops / sec / 1e12},
+            "heavy_ball": {"ms_per_iter": sec_hb * 1e3, "iter_per_s": 1.0 / sec_hb,
+                           "achieved_gbs": 2 * info["q_bytes"] / sec_hb / 1e9,
+                           "frac": 2 * info["q_bytes"] / sec_hb / 1e9 / peak,
+                           "algorithmic_bytes_per_iter": 2 * info["q_bytes"]}}
 
 
 def run_ours(args):
