@@ -53,6 +53,7 @@ __all__ = [
     "apc_forward_linear", "apc_adjoint", "power_mu_max", "ApcTrace",
     "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine", "partition_rows",
     "precondition_blocks", "hb_optimal_params", "dhbm_step", "dhbm_run",
+    "rate_dgd", "rate_dnag", "rate_dhbm", "madmm_step", "madmm_rate", "madmm_optimal_rate", "table2_row",
 ]
 
 
@@ -306,6 +307,74 @@ def rate_cimmino(kappa_X: float) -> float:
 def rate_consensus(mu_min: float) -> float:
     """Standard projection consensus (gamma = eta = 1), Table 1: 1 - mu_min(X)."""
     return 1.0 - mu_min
+
+
+def rate_dgd(kappa_AtA: float) -> float:
+    """Distributed gradient descent, optimal step (Sec. 4.1): (kappa - 1)/(kappa + 1)."""
+    return (kappa_AtA - 1.0) / (kappa_AtA + 1.0)
+
+
+def rate_dnag(kappa_AtA: float) -> float:
+    """Distributed Nesterov accelerated gradient, optimal tuning (Sec. 4.2):
+    1 - 2 / sqrt(3 kappa + 1)."""
+    return 1.0 - 2.0 / math.sqrt(3.0 * kappa_AtA + 1.0)
+
+
+def rate_dhbm(kappa_AtA: float) -> float:
+    """Distributed heavy ball, optimal tuning (Sec. 4.3): (sqrt(kappa) - 1)/(sqrt(kappa) + 1)."""
+    s = math.sqrt(kappa_AtA)
+    return (s - 1.0) / (s + 1.0)
+
+
+def madmm_step(blocks, xbar: np.ndarray, xi: float) -> np.ndarray:
+    """One iteration of the modified consensus ADMM of Sec. 4.4 (the y_i set to
+    zero): x_i = (A_i^T A_i + xi I)^{-1} (A_i^T b_i + xi xbar), xbar' = mean_i x_i."""
+    n = xbar.shape[0]
+    xs = [np.linalg.solve(A_i.T @ A_i + xi * np.eye(n), A_i.T @ b_i + xi * xbar) for A_i, b_i in blocks]
+    return sum(xs) / len(xs)
+
+
+def madmm_rate(blocks, xi: float) -> float:
+    """Rate of ``madmm_step``: the error map is e -> (1/m) sum_i xi (A_i^T A_i + xi I)^{-1} e
+    (subtract the step at the solution), so the rate is its largest eigenvalue."""
+    n = blocks[0][0].shape[1]
+    M = sum(xi * np.linalg.inv(A_i.T @ A_i + xi * np.eye(n)) for A_i, _ in blocks) / len(blocks)
+    return float(np.linalg.eigvalsh((M + M.T) / 2).max())
+
+
+def madmm_optimal_rate(blocks, lo: float = -4.0, hi: float = 6.0, points: int = 41) -> tuple[float, float]:
+    """The paper tunes every method to its best parameter (Sec. 5); Sec. 4.4
+    gives no closed form for the modified ADMM, so scan ``madmm_rate`` over
+    xi = 10^lo .. 10^hi (log grid) and return the best (xi, rate).  Each term
+    xi (A_i^T A_i + xi I)^{-1} grows with xi in the Loewner order, so the best
+    rate is approached as xi -> 0, where the error map tends to
+    (1/m) sum_i P_i = I - X (Sec. 3.2): the consensus rate 1 - mu_min(X).
+    (Below xi ~ 1e-4 the inverse of A_i^T A_i + xi I is too ill-conditioned for
+    FP64 to resolve the rate; the default grid stops there.)"""
+    best = (0.0, 2.0)
+    for e in np.linspace(lo, hi, points):
+        r = madmm_rate(blocks, 10.0 ** e)
+        if r < best[1]:
+            best = (10.0 ** e, r)
+    return best
+
+
+def table2_row(A: np.ndarray, b: np.ndarray, row_offsets) -> dict:
+    """Convergence times T = 1/(-log rho) of the methods compared in Table 2
+    (Sec. 5) for one problem, from the rates of Table 1 (and ``madmm_optimal_rate``):
+    the spectra of A^T A = sum_i A_i^T A_i and of X decide them all."""
+    blocks = partition(A, b, row_offsets)
+    Qs = [block_qr(A_i)[0] for A_i, _ in blocks]
+    mu_lo, mu_hi = mu_bounds(Qs)
+    sv = np.linalg.svd(A, compute_uv=False)
+    k_ata = float((sv.max() / sv.min()) ** 2)
+    k_x = mu_hi / mu_lo
+    _, r_admm = madmm_optimal_rate(blocks)
+    rates = {"DGD": rate_dgd(k_ata), "D-NAG": rate_dnag(k_ata), "D-HBM": rate_dhbm(k_ata), "M-ADMM": r_admm,
+             "B-Cimmino": rate_cimmino(k_x), "APC": rate_apc(k_x), "Consensus": rate_consensus(mu_lo)}
+    out = {k: convergence_time(r) for k, r in rates.items()}
+    out.update(kappa_AtA=k_ata, kappa_X=k_x, mu_min=mu_lo, mu_max=mu_hi)
+    return out
 
 
 def convergence_time(rho: float) -> float:

@@ -42,11 +42,11 @@ def uneven_offsets(N: int, p_lo: int, p_hi: int, rng: np.random.Generator) -> np
     return np.asarray(offs, dtype=np.int64)
 
 
-def gaussian_system(n: int, seed: int, N: int | None = None, k: int = 1):
-    """(A, x_true, b): A N x n i.i.d. N(0,1), x_true n (x k) ~ N(0,1), b = A x_true."""
+def gaussian_system(n: int, seed: int, N: int | None = None, k: int = 1, mean: float = 0.0):
+    """(A, x_true, b): A N x n i.i.d. N(mean, 1), x_true n (x k) ~ N(0,1), b = A x_true."""
     rng = np.random.default_rng(seed)
     N = n if N is None else N
-    A = rng.standard_normal((N, n))
+    A = rng.standard_normal((N, n)) + mean
     x_true = rng.standard_normal((n,) if k == 1 else (n, k))
     return A, x_true, A @ x_true
 
