@@ -55,7 +55,8 @@ constexpr int kMinStages = 5;
 size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster);
 constexpr int kRowsPerGroup = 2;   // rows of Q per pipeline step
 constexpr int kMaxElemWarps = 16;  // warps streaming Q per CTA of the iteration kernel
-constexpr int kCtlWarps = 2;       // control warps per CTA (one per row of a group)
+constexpr int kCtlWarps = 4;       // control warps per CTA: per row of a group, one for the
+                                   // master's update and one for the machines' update
 constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps) * 32;
 
 // Kernel entry points, one translation unit per Q precision.

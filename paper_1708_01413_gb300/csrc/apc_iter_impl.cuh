@@ -54,13 +54,19 @@ namespace iterk {
 
 constexpr int R = kRowsPerGroup;   // rows per group (= 2, hard-wired below)
 static_assert(R == 2, "the transposed butterfly and lane roles assume 2 rows per group");
-constexpr int NX = 4;              // cluster exchange buffers (groups in flight)
+// Cluster exchange buffers (groups in flight).  A peer writes group g + NX's
+// row sums into the slot of group g only after its master has seen this CTA's
+// sums of group g + NX - 2, which this CTA's update warps send in step
+// t + NX - 2; this CTA's master reads group g in step t + 2.  NX >= 5 keeps the
+// read before the overwrite (and one mbarrier phase per slot in flight).
+constexpr int NX_LOG2 = 3;
+constexpr int NX = 1 << NX_LOG2;
 constexpr int DELAY = 2;           // steps between a group's first and second product
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct SmemLayout {
-    size_t stage_elems, row_stride, off_xb, off_d, off_coef, off_sloc, off_bars, total;
+    size_t stage_elems, row_stride, off_xb, off_d, off_coef, off_sloc, off_xh, off_bars, total;
     __host__ __device__ SmemLayout(size_t q_elem, size_t s_elem, int slots, int P, int stages, int64_t rpc) {
         row_stride = size_t(slots) * P;               // elements per staged row
         stage_elems = size_t(R) * row_stride;
@@ -70,7 +76,8 @@ struct SmemLayout {
         off_d = align_up(off_xb + 2 * size_t(rpc) * 8, 16);        // first-product results [2][R][32]
         off_coef = align_up(off_d + 2 * R * 32 * s_elem, 16);      // second-product coefficients [2][32][R]
         off_sloc = align_up(off_coef + 2 * 32 * R * s_elem, 16);   // cluster row sums [NX][8][R]
-        off_bars = align_up(off_sloc + size_t(NX) * 8 * R * 8, 8);
+        off_xh = align_up(off_sloc + size_t(NX) * 8 * R * 8, 16);  // machines' x_i' by group [4][R][32]
+        off_bars = align_up(off_xh + size_t(4) * R * 32 * s_elem, 8);
         total = off_bars + (stages + NX) * sizeof(uint64_t);
     }
 };
@@ -259,16 +266,23 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     TS *dsh = reinterpret_cast<TS *>(smem + L.off_d);           // [2][R][32]  w_i[j] from the first product
     TS *coefs = reinterpret_cast<TS *>(smem + L.off_coef);      // [2][32][R]  coefficients of the second product
     uint64_t *sloc = reinterpret_cast<uint64_t *>(smem + L.off_sloc);  // [NX][8][R] cluster row sums
+    TS *xhist = reinterpret_cast<TS *>(smem + L.off_xh);               // [4][R][32] x_i' of recent groups
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L.off_bars);  // [S]
     uint64_t *xchg = full + S;                                          // [NX]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // Warps [0, nwe) stream Q (both products).  Warp nwe + r ("control warp r")
-    // owns row r of each group: lane s handles worker slot s -- the machines'
-    // updates, the CTA row sum, the cluster exchange, the master's update and
-    // the second product's coefficients.  Lane 0 of control warp 1 issues TMA.
+    // Warps [0, nwe) stream Q (both products).  Four control warps own the
+    // rows of a group; lane s handles worker slot s.  Control warp r (r < R)
+    // runs the master's update of row r of group t-2 and the second product's
+    // coefficients; control warp R + r runs the machines' updates of row r of
+    // group t, the CTA row sum and the cluster exchange.  The two chains are
+    // independent within a step (they meet through shared memory two steps
+    // apart), so a step waits for the longer of them, not their sum.  Lane 0
+    // of control warp 1 issues TMA.
     const bool is_ctl = warp >= nwe;
     const int ctl_r = warp - nwe;
+    const int ctl_row = ctl_r & 1;
+    const bool ctl_master = is_ctl && ctl_r < R;
     const int issuer = (nwe + 1) * 32;
     const uint32_t rank = cluster_rank();
     const int cl = int(cluster_id_x());
@@ -373,12 +387,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     const bool c_act = is_ctl && lane < W_cta;
     TS *const cx0 = xw + size_t(row0 + (ctl_r & 1)) * m + lane;
     const size_t xstep = size_t(R) * m;
-    const bool cx_ok = rx && c_act;
+    const bool cx_ok = rx && c_act && !ctl_master;
     TS *cx_next = cx0;
     int k_next = 0;
     auto cx_load_next = [&]() -> TS {
         TS v = TS(0);
-        if (cx_ok && k_next * R + ctl_r < nrows) v = *cx_next;
+        if (cx_ok && k_next * R + ctl_row < nrows) v = *cx_next;
         if (++k_next == G) {
             k_next = 0;
             cx_next = cx0;
@@ -387,10 +401,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         }
         return v;
     };
-    TS cxpre = (is_ctl && G > 0) ? cx_load_next() : TS(0);
+    TS cxpre = (is_ctl && !ctl_master && G > 0) ? cx_load_next() : TS(0);
     TS *cx_cur = cx0;
-    TS xh0 = TS(0), xh1 = TS(0), xh2 = TS(0);  // this lane's x_i' of groups t, t-1, t-2
-    int nrh1 = 0, nrh2 = 0;                     // row counts of groups t-1, t-2
 
     uint32_t sb1 = 0, sb2 = 0;  // stage byte offsets: first product (group t), second (group t-3)
     int st1 = 0, ph1 = 0;
@@ -471,10 +483,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 ph1 ^= 1;
             }
             sb1 = uint32_t(st1) * stage_bytes;
-        } else if (ctl_r < R) {
-            const int r = ctl_r;
+        } else {
+            const int r = ctl_row;
             if (e1 && tid == issuer && W_cta > 0 && issued < total) issue_next();
-            if (mm) {
+            const int nrh2 = (t >= 2 && t - 2 < G) ? min(R, nrows - (t - 2) * R) : 0;
+            if (ctl_master && mm) {
                 // ---- master of row r of group t-2: cluster row sums -> new xbar, coefficients ----
                 const int g2 = g - 2;
                 const int bx = g2 & (NX - 1);
@@ -482,7 +495,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 if constexpr (kDF) {
                     float2 xnew = make_float2(0.0f, 0.0f);
                     if (lane == 0) {
-                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> 2) & 1), a.timeout_ns)) {
+                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> NX_LOG2) & 1), a.timeout_ns)) {
                             abort_flag = 1;
                             abort_code = DEV_TIMEOUT_XCHG;
                         }
@@ -499,12 +512,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                     }
                     xnew.x = __shfl_sync(0xffffffffu, xnew.x, 0);
                     xnew.y = __shfl_sync(0xffffffffu, xnew.y, 0);
+                    const TS xh2 = xhist[((g2 & 3) * R + r) * 32 + lane];
                     const TS c = (r < nrh2 && lane < W_cta) ? TS((xnew.x - float(xh2)) + xnew.y) : TS(0);
                     coefs[((g2 & 1) * 32 + lane) * R + r] = c;
                 } else {
                     double xnew = 0.0;
                     if (lane == 0) {
-                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> 2) & 1), a.timeout_ns)) {
+                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> NX_LOG2) & 1), a.timeout_ns)) {
                             abort_flag = 1;
                             abort_code = DEV_TIMEOUT_XCHG;
                         }
@@ -521,12 +535,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                         }
                     }
                     xnew = __shfl_sync(0xffffffffu, xnew, 0);
+                    const TS xh2 = xhist[((g2 & 3) * R + r) * 32 + lane];
                     const TS c = (r < nrh2 && lane < W_cta)
                                      ? TS(Row::coef(mode, double(xh2), xnew, a.eta, a.inv_m)) : TS(0);
                     coefs[((g2 & 1) * 32 + lane) * R + r] = c;
                 }
             }
-            if (e1) {
+            if (!ctl_master && e1) {
                 // ---- machines' updates of row r of group t and the CTA row sum ----
                 TS xn = TS(0), contrib = TS(0);
                 if (r < nr && c_act) {
@@ -551,7 +566,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 // group per pass the next group is the same rows)
                 cxpre = cx_load_next();
                 cx_cur = (t + 1 < G) ? cx_cur + xstep : cx0;
-                xh0 = xn;
+                xhist[((g & 3) * R + r) * 32 + lane] = xn;  // read by the master's warp two steps later
                 const int bx = g & (NX - 1);
                 uint64_t payload;
                 if constexpr (kF64) {
@@ -583,12 +598,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                     mbar_arrive_expect_tx(&xchg[bx], r < nr ? uint32_t((cs - 1) * 8) : 0u);
                 }
             }
-            // this lane's history: group t becomes t-1, t-1 becomes t-2
-            xh2 = xh1;
-            xh1 = e1 ? xh0 : TS(0);
-            xh0 = TS(0);
-            nrh2 = nrh1;
-            nrh1 = nr;
         }
         return false;
     };
