@@ -287,3 +287,34 @@ def test_batch_heavy_ball_reaches_the_bf16_fixed_point():
     bt.reset()
     bt.iterate(T)
     assert _rel(bt.xbar(0).cpu().numpy(), x_fp) <= 1e-5
+
+
+@pytest.mark.parametrize("seed", [101, 102, 103])
+def test_batch_random_shapes_match_oracle(seed):
+    # random mixes: tiny and mid-size systems, blocks from 1 row up to 128 rows
+    # (widths that are and are not multiples of 8 and 16), ragged k
+    apc, dev = _apc(), _dev()
+    rng = np.random.default_rng(seed)
+    k = int(rng.choice([1, 3, 16, 17, 32]))
+    systems = []
+    for _ in range(int(rng.integers(2, 6))):
+        n = int(rng.integers(17, 700))
+        A = rng.standard_normal((n, n)) + np.sqrt(n) * np.eye(n)
+        B = rng.standard_normal((n, k))
+        offs = inputs.uneven_offsets(n, 1, min(128, n - 1), rng)
+        systems.append((A, B, offs))
+    T = 10
+    refs, params = [], []
+    for A, B, offs in systems:
+        Qs, Rs, cs = _oracle_system(A, B, offs)
+        g, e, _ = O.optimal_params(*O.mu_bounds(Qs))
+        params.append((g, e))
+        refs.append(O.apc_run_affine([O.round_bf16(Q) for Q in Qs], cs, g, e, T)[1])
+    bt = apc.apc_batch_setup([torch.tensor(A, device=dev) for A, _, _ in systems],
+                             [torch.tensor(B, device=dev) for _, B, _ in systems],
+                             [offs for _, _, offs in systems])
+    bt.set_params([p[0] for p in params], [p[1] for p in params])
+    bt.reset()
+    bt.iterate(T)
+    for s, ref in enumerate(refs):
+        assert _rel(bt.xbar(s).cpu().numpy().reshape(ref.shape), ref) <= TOL, (s, k)
