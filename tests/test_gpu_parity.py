@@ -295,3 +295,54 @@ def test_device_wait_timeout_is_reported_and_context_recovers():
     ctx.iterate(g, e, T)
     ref = O.apc_run(A, b, offs, g, e, max_iters=T, Qs=Qs, Rs=Rs)
     assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-5
+
+
+def test_differentiation_workload_full_size():
+    # A 8192 x 8192 Gaussian, m = 32 blocks of 256, k = 16 right-hand sides,
+    # L = 0.5 ||xbar_T - x_target||^2 through T = 200 unrolled iterations.
+    # The map b -> xbar_T is linear and L quadratic, so central differences of
+    # the FP64 forward are exact up to rounding: the FP32 autograd gradient is
+    # checked against them (1e-4), and the FP64 forward / reverse sweep pass the
+    # dot-product test <J v, w> = <v, J^T w>.  (gamma, eta) from the GPU
+    # spectral estimates.
+    apc, dev = _apc(), _dev()
+    n, m, k, T = 8192, 32, 16, 200
+    A, _, _ = inputs.gaussian_system_torch(n, 77, dev)
+    g_ = torch.Generator(device=dev)
+    g_.manual_seed(78)
+    B = torch.randn((n, k), generator=g_, device=dev, dtype=torch.float64)
+    xt = torch.randn((n, k), generator=g_, device=dev, dtype=torch.float64)
+    offs = inputs.even_offsets(n, m)
+    c64 = apc.apc_setup(A, B[:, 0].contiguous(), offs, precision="f64")
+    c32 = apc.apc_setup(A, B[:, 0].contiguous(), offs, precision="f32")
+    lo, hi = c64.spectral_bounds(steps=60, seed=5)
+    gam, eta, _ = apc.apc_optimal_params(0.5 * lo, min(1.0, 1.01 * hi))
+
+    def forward(ctx, Bm):
+        cols = []
+        for j in range(Bm.shape[1]):
+            ctx.reset(Bm[:, j].contiguous())
+            ctx.iterate(gam, eta, T)
+            cols.append(ctx.xbar().clone())
+        return torch.stack(cols, dim=1)
+
+    bt = B.clone().requires_grad_(True)
+    x = apc.APCSolveFn.apply(bt, c32, gam, eta, T)
+    loss = 0.5 * ((x - xt) ** 2).sum()
+    loss.backward()
+    grad = bt.grad
+    D = torch.randn((n, k), generator=g_, device=dev, dtype=torch.float64)
+    h = 1e-2 * float(torch.linalg.norm(B))
+
+    def L(Bm):
+        return 0.5 * float(((forward(c64, Bm) - xt) ** 2).sum())
+
+    fd = (L(B + h * D) - L(B - h * D)) / (2 * h)
+    assert float((grad * D).sum()) == pytest.approx(fd, rel=1e-4)
+    # dot-product test of the FP64 forward and reverse sweeps (one column)
+    v = torch.randn(n, generator=g_, device=dev, dtype=torch.float64)
+    w = torch.randn(n, generator=g_, device=dev, dtype=torch.float64)
+    Jv = forward(c64, v.unsqueeze(1))[:, 0]
+    JTw = c64.backward(w, T, gam, eta)
+    lhs, rhs = float(Jv @ w), float(v @ JTw)
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), abs(rhs))
