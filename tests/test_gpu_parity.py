@@ -346,3 +346,51 @@ def test_differentiation_workload_full_size():
     JTw = c64.backward(w, T, gam, eta)
     lhs, rhs = float(Jv @ w), float(v @ JTw)
     assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), abs(rhs))
+
+
+@pytest.mark.parametrize("name,n,m,prec", [("scaled 32768, BF16", 32768, 128, "bf16"),
+                                           ("Gaussian 16384, FP32", 16384, 64, "f32")])
+def test_full_size_workloads_sampled_and_properties(name, n, m, prec):
+    # The benchmark's workloads in its launch configuration.  Sampled outputs
+    # the oracle computes one by one from its own QR of every block: xbar(0) at
+    # 48 rows (least-norm start, bases rounded like the stored ones).  After 20
+    # iterations, properties that hold at any size: the master's update
+    # (Eq. (cons2)) recomputed in FP64 from the machines' iterates, and every
+    # machine's step lies in the nullspace of its block (Sec. 3.1:
+    # A_i (x_i(t+1) - x_i(t)) = gamma A_i P_i (...) = 0), up to the precision of
+    # the stored basis.
+    apc, dev = _apc(), _dev()
+    if prec == "bf16":
+        A, _, b = inputs.scaled_system_torch(n, 1234, dev)
+        rnd = O.round_bf16
+    else:
+        A, _, b = inputs.gaussian_system_torch(n, 1235, dev)
+        rnd = lambda q: q.astype(np.float32).astype(np.float64)  # noqa: E731
+    offs = inputs.even_offsets(n, m)
+    ctx = apc.apc_setup(A, b, offs, precision=prec)
+    ctx.reset()
+    x0 = ctx.xbar().cpu().numpy()
+    rng = np.random.default_rng(5)
+    J = np.sort(rng.choice(n, 48, replace=False))
+    bh = b.cpu().numpy()
+    want = np.zeros(len(J))
+    for i in range(m):
+        Ai = A[offs[i]:offs[i + 1]].cpu().numpy()
+        Q, R = O.block_qr(Ai)
+        c = O.block_coefficients(Q, R, bh[offs[i]:offs[i + 1]])
+        want += rnd(Q[J]) @ c
+    want /= m
+    assert _rel(x0[J], want) <= 1e-5, name
+    gam, eta = 1.0, 1.5
+    ctx.iterate(gam, eta, 20)
+    xs0, xb0 = ctx.x(), ctx.xbar().clone()
+    ctx.iterate(gam, eta, 1)
+    xs1, xb1 = ctx.x(), ctx.xbar()
+    master = eta / m * xs1.sum(dim=0) + (1.0 - eta) * xb0
+    assert float(torch.linalg.norm(xb1 - master) / torch.linalg.norm(xb1)) <= 1e-6, name
+    tol = 2e-2 if prec == "bf16" else 1e-5
+    for i in rng.choice(m, 6, replace=False):
+        Ai = A[offs[i]:offs[i + 1]]
+        dx = xs1[i] - xs0[i]
+        ratio = float(torch.linalg.norm(Ai @ dx) / (torch.linalg.norm(Ai) * torch.linalg.norm(dx)))
+        assert ratio <= tol, (name, int(i), ratio)
