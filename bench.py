@@ -18,6 +18,9 @@ Also on the same JSON line:
                Gaussian system (2304 x 2048, 9 blocks of 256, kappa(X) ~ 1e3): the
                32768 scaled matrix has kappa(X) ~ 1e12 and needs far more
                iterations than a benchmark can run;
+  tts_n32768   the same comparison at the headline size on a tall Gaussian
+               system (36864 x 32768, 144 blocks of 256, kappa(X) ~ 1e3), with
+               the spectrum estimated on the GPU (Lanczos);
   batch        the batched solver on 256 independent systems (n ~ U{256..4096},
                A = G + 0.5 sqrt(n) I, blocks p_i ~ U{16..128}, k = 32
                right-hand sides, BF16 bases): iterations per second of the
@@ -264,6 +267,52 @@ def time_to_tolerance(dev, tol=1e-10):
     return out
 
 
+def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
+    """Time to relative residual `tol` at the headline size: a tall Gaussian
+    system (N = 36864 equations, n = 32768 unknowns, 144 blocks of 256; kappa(X)
+    stays ~1e3 at any size for this aspect ratio), BF16 + FP64 refinement
+    against FP32 + FP64 refinement, plus the residual plain FP32 reaches in a
+    bounded run.  Each context estimates the extreme eigenvalues of its own X
+    with the GPU Lanczos (apc_spectral_bounds), margins 0.98 / 1.01, then
+    Theorem 1's (gamma, eta).  `seconds` covers the solve alone (set-up and
+    Lanczos are reported beside it)."""
+    import torch
+    from paper_1708_01413_gb300 import apc, inputs
+    m = N // p
+    A, x_true, b = inputs.gaussian_system_torch(n, 13, dev, N=N)
+    offs = inputs.even_offsets(N, m)
+    out = {"workload": f"tall Gaussian N={N}, n={n}, m={m} blocks of {p}", "tol": tol}
+    runs = (("bf16_ir", "bf16", True, 5000), ("f32_ir", "f32", True, 5000), ("f32_plain", "f32", False, 2000))
+    for key, prec, refine, max_iters in runs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = apc.apc_setup(A, b, offs, precision=prec)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        try:
+            t0 = time.perf_counter()
+            lo, hi = ctx.spectral_bounds(steps=150)
+            t_lanczos = time.perf_counter() - t0
+            g, e, rho = apc.apc_optimal_params(0.98 * lo, min(1.0, 1.01 * hi))
+            ctx.solve(g, e, tol=tol, max_iters=100, check_every=50, refine=refine, raise_on_error=False)  # warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, st = ctx.solve(g, e, tol=tol, max_iters=max_iters, check_every=50, refine=refine,
+                              raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[key] = {"seconds": dt, "iterations": st["iterations"], "sweeps": st["sweeps"],
+                        "rel_residual": st["rel_residual"],
+                        "rel_error": float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)),
+                        "converged": st["rc"] == 0, "mu_bounds": [lo, hi], "kappa_X": hi / lo, "rho": rho,
+                        "setup_s": round(t_setup, 3), "lanczos_s": round(t_lanczos, 3)}
+        finally:
+            ctx.close()
+    del A, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
     """The FP32 path (Q in FP32) on the same matrix: iterations/s and HBM GB/s."""
     import torch
@@ -450,6 +499,10 @@ def run_ours(args):
             extra["tts"] = time_to_tolerance(dev)
         except Exception as exc:
             extra["tts"] = {"error": str(exc)}
+        try:
+            extra["tts_n32768"] = time_to_tolerance_large(dev)
+        except Exception as exc:
+            extra["tts_n32768"] = {"error": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -70,8 +70,12 @@ int configure(apc_ctx *c, int cs_request, int wpw_request) {
     const int R = kRowsPerGroup;
     const size_t qsz = q_elem_size(c->precision);
     const size_t budget = size_t(smem_optin) - 2 * 1024;
-    const int cands[4] = {1, 2, 4, 8};
-    for (int ci = 0; ci < 4; ++ci) {
+    // The smallest cluster whose CTAs hold at most 32 worker slots each: fewer
+    // CTAs per row range means fewer cluster exchanges per row and more work
+    // per pipeline step (sizes need not be powers of two; 8 is the portable
+    // maximum).
+    const int cands[8] = {1, 2, 3, 4, 5, 6, 7, 8};
+    for (int ci = 0; ci < 8; ++ci) {
         const int cs = cands[ci];
         if (cs_request > 0 && cs != cs_request) continue;
         const int W0 = (c->m + cs - 1) / cs;

@@ -87,12 +87,15 @@ def target_vector(n: int, seed: int, k: int = 1) -> np.ndarray:
 # the given device; results differ from the NumPy streams above, so a test
 # that compares against the oracle copies the device arrays back to the host.
 
-def gaussian_system_torch(n: int, seed: int, device, dtype=None):
+def gaussian_system_torch(n: int, seed: int, device, dtype=None, N: int | None = None):
+    """(A, x_true, b) on the device: A N x n (N = n by default) i.i.d. N(0,1),
+    x_true ~ N(0,1), b = A x_true."""
     import torch
     dtype = torch.float64 if dtype is None else dtype
+    N = n if N is None else N
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    A = torch.randn((n, n), generator=g, device=device, dtype=dtype)
+    A = torch.randn((N, n), generator=g, device=device, dtype=dtype)
     x_true = torch.randn((n,), generator=g, device=device, dtype=dtype)
     return A, x_true, A @ x_true
 

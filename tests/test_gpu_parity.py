@@ -126,6 +126,25 @@ def test_cluster_sizes_agree(cs, wpw):
     assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-5
 
 
+@pytest.mark.parametrize("cs,m", [(3, 16), (5, 18), (6, 22), (7, 26), (0, 144)])
+def test_cluster_sizes_not_powers_of_two(cs, m):
+    # clusters of 3, 5, 6 and 7 CTAs (the last CTA of each holds fewer
+    # workers), and the automatic choice for m = 144 blocks (5 CTAs of <= 30
+    # worker slots) give the oracle's trajectory.  FP64 path (the same kernel
+    # template), so that an exchange error cannot hide under FP32 rounding,
+    # which at m = 144 (eta ~ 145) already moves the trajectory by ~5e-5.
+    apc, dev = _apc(), _dev()
+    n, T = (2304 if m == 144 else 1200), 30
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 5)
+    ref = O.apc_run(A, b, offs, g, e, max_iters=T, Qs=Qs, Rs=Rs)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64",
+                        cluster_size=cs)
+    assert ctx.info()["cluster_size"] == (cs if cs else 5)
+    ctx.reset()
+    ctx.iterate(g, e, T)
+    assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-10
+
+
 def test_bf16_trajectory_close_to_oracle():
     apc, dev = _apc(), _dev()
     n, m, T = 2048, 8, 20
