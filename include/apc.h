@@ -80,7 +80,8 @@ typedef struct apc_stats {
  *   b_dev  : N, FP64, device.
  *   N >= n >= 1; row_offsets_host: m+1 strictly increasing int64 with
  *   offsets[0] = 0 and offsets[m] = N; every block has 1..256 rows and
- *   fewer rows than n.  m <= 256.
+ *   at most n rows (a block of n rows of a square system is the whole
+ *   system: P_1 = 0).  m <= 256.
  * Errors: INVALID_ARG, SINGULAR_BLOCK (block index in apc_last_error),
  * NONFINITE, NOMEM, CUDA, UNSUPPORTED.  On error *out is NULL. */
 int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t lda,

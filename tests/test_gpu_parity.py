@@ -86,6 +86,43 @@ def test_f64_trajectory_matches_oracle(n, m, T):
         assert _rel(X[i], ref.xs[i]) <= 1e-10
 
 
+@pytest.mark.parametrize("n,offs", [(1, [0, 1]), (2, [0, 1, 2]), (3, [0, 1, 2, 3]), (5, [0, 2, 5]),
+                                    (64, [0, 1, 2, 10, 11, 40, 64]), (70, [0, 70]), (256, [0, 256])])
+def test_degenerate_shapes_f64(n, offs):
+    # 1 x 1 to 5 x 5 systems (fewer rows than one pipeline group per cluster,
+    # a one-row last group), 1-row blocks, and a single block holding the
+    # whole square system (P_1 = 0: the least-norm start is the solution and
+    # the iteration leaves it there); zero iterations change nothing
+    apc, dev = _apc(), _dev()
+    offs = np.asarray(offs, dtype=np.int64)
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, len(offs) - 1, 12, offs=offs)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64")
+    ctx.reset()
+    x0 = ctx.xbar().cpu().numpy()
+    ref0 = sum(O.least_norm_init(Q, R, bi) for Q, R, (_, bi) in zip(Qs, Rs, blocks)) / len(blocks)
+    assert _rel(x0, ref0) <= 1e-12
+    ctx.iterate(g, e, 0)
+    assert np.array_equal(ctx.xbar().cpu().numpy(), x0)
+    T = 40
+    ref = O.apc_run(A, b, offs, g, e, max_iters=T, Qs=Qs, Rs=Rs)
+    ctx.iterate(g, e, T)
+    assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-10
+    if len(offs) == 2:
+        assert _rel(ctx.xbar().cpu().numpy(), x_true) <= 1e-9
+
+
+def test_block_wider_than_256_rows_is_unsupported():
+    apc, dev = _apc(), _dev()
+    A, _, b = inputs.gaussian_system(300, 13)
+    with pytest.raises(apc.ApcError) as ei:
+        apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), [0, 257, 300], precision="f64")
+    assert ei.value.name == "UNSUPPORTED"
+    with pytest.raises(apc.ApcError) as ei:  # more rows than unknowns: rank-deficient block
+        Bt, _, bt = inputs.gaussian_system(40, 13, N=90)
+        apc.apc_setup(torch.tensor(Bt, device=dev), torch.tensor(bt, device=dev), [0, 45, 90], precision="f64")
+    assert ei.value.name == "SINGULAR_BLOCK"
+
+
 def test_f64_solve_config1_reaches_lu_solution():
     # 500 x 500 Gaussian, m = 10 blocks of 50 rows, optimal (gamma, eta), tol 1e-10
     apc, dev = _apc(), _dev()
