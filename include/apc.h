@@ -61,6 +61,7 @@ typedef struct apc_options {
     int32_t cluster_size;   /* CTAs sharing one row range, 1..8; 0 = automatic */
     int32_t workers_per_warp; /* 1 or 2 blocks per warp; 0 = automatic        */
     double  timeout_s;      /* limit of every device-side wait; 0 = 2 s       */
+    int32_t rows_per_group; /* rows of Q per pipeline step, 1 or 2; 0 = automatic */
 } apc_options;
 
 typedef struct apc_stats {
@@ -228,9 +229,10 @@ int apc_backward(apc_ctx *ctx, const double *g_dev, int64_t T, double gamma, dou
 int apc_set_test_hooks(apc_ctx *ctx, int32_t grid_barrier_skew, double timeout_s);
 
 /* apc_context_info -- sizes chosen at setup: padded block width, cluster
- * size, number of clusters and bytes of Q.  Any pointer may be NULL. */
+ * size, number of clusters, bytes of Q and rows of Q per pipeline step.  Any
+ * pointer may be NULL. */
 int apc_context_info(const apc_ctx *ctx, int64_t *n, int64_t *N, int32_t *m, int32_t *width,
-                     int32_t *cluster_size, int32_t *clusters, int64_t *q_bytes);
+                     int32_t *cluster_size, int32_t *clusters, int64_t *q_bytes, int32_t *rows_per_group);
 
 /* apc_last_error -- text of the last error on ctx (or of the last failed
  * apc_setup when ctx is NULL).  Valid until the next call on ctx. */

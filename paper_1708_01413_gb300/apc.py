@@ -41,7 +41,7 @@ class ApcError(RuntimeError):
 
 class apc_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("cluster_size", C.c_int32), ("workers_per_warp", C.c_int32),
-                ("timeout_s", C.c_double)]
+                ("timeout_s", C.c_double), ("rows_per_group", C.c_int32)]
 
 
 class apc_stats(C.Structure):
@@ -74,7 +74,7 @@ def lib() -> C.CDLL:
     L.apc_residual.argtypes = [vp, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_solve.argtypes = [vp, dbl, dbl, dbl, i64, i64, i32, vp, C.POINTER(apc_stats), vp]
     L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
-                                   C.POINTER(i32), C.POINTER(i32), C.POINTER(i64)]
+                                   C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
     L.apc_backward.argtypes = [vp, vp, i64, dbl, dbl, vp, vp]
     L.apc_set_test_hooks.argtypes = [vp, i32, dbl]
     L.apc_spectral_bounds.argtypes = [vp, i32, C.c_uint64, C.POINTER(dbl), C.POINTER(dbl), vp]
@@ -158,11 +158,11 @@ class Context:
 
     def info(self) -> dict:
         n, N, cb = C.c_int64(), C.c_int64(), C.c_int64()
-        m, w, cs, cl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        m, w, cs, cl, rg = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().apc_context_info(self.handle, C.byref(n), C.byref(N), C.byref(m), C.byref(w),
-                                      C.byref(cs), C.byref(cl), C.byref(cb)), self.handle)
+                                      C.byref(cs), C.byref(cl), C.byref(cb), C.byref(rg)), self.handle)
         return dict(n=n.value, N=N.value, m=m.value, width=w.value, cluster_size=cs.value,
-                    clusters=cl.value, q_bytes=cb.value)
+                    clusters=cl.value, q_bytes=cb.value, rows_per_group=rg.value)
 
     def reset(self, rhs=None, stream=None):
         _check(lib().apc_reset(self.handle, _ptr(rhs), _stream(stream)), self.handle)
@@ -292,7 +292,7 @@ def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:
 
 
 def apc_setup_rows(A, b, row_sets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,
-                   workers_per_warp=0) -> Context:
+                   workers_per_warp=0, rows_per_group=0) -> Context:
     """Factor a partition whose blocks are arbitrary row sets: block i holds
     the rows ``row_sets[i]`` of A (FP64 CUDA tensor, N x n) and b."""
     import numpy as np
@@ -306,7 +306,7 @@ def apc_setup_rows(A, b, row_sets, precision="f32", cluster_size=0, timeout_s=0.
     index = np.ascontiguousarray(np.concatenate(sets))
     offs = np.ascontiguousarray(np.concatenate([[0], np.cumsum([len(r) for r in sets])]).astype(np.int64))
     opt = apc_options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                      int(cluster_size), int(workers_per_warp), float(timeout_s))
+                      int(cluster_size), int(workers_per_warp), float(timeout_s), int(rows_per_group))
     h = C.c_void_p()
     with torch.cuda.device(A.device):
         rc = lib().apc_setup_rows(C.byref(h), _ptr(A), A.shape[0], A.shape[1], A.stride(0), _ptr(b),
@@ -318,7 +318,7 @@ def apc_setup_rows(A, b, row_sets, precision="f32", cluster_size=0, timeout_s=0.
 
 
 def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0, stream=None,
-              workers_per_warp=0) -> Context:
+              workers_per_warp=0, rows_per_group=0) -> Context:
     """Factor the row blocks of A (FP64 CUDA tensor, N x n) for right-hand side b."""
     import numpy as np
     import torch
@@ -330,7 +330,7 @@ def apc_setup(A, b, row_offsets, precision="f32", cluster_size=0, timeout_s=0.0,
     offs = np.ascontiguousarray(np.asarray(row_offsets, dtype=np.int64))
     m = len(offs) - 1
     opt = apc_options(PRECISIONS[precision] if isinstance(precision, str) else int(precision),
-                      int(cluster_size), int(workers_per_warp), float(timeout_s))
+                      int(cluster_size), int(workers_per_warp), float(timeout_s), int(rows_per_group))
     h = C.c_void_p()
     with torch.cuda.device(A.device):
         rc = lib().apc_setup(C.byref(h), _ptr(A), A.shape[0], A.shape[1], A.stride(0), _ptr(b),

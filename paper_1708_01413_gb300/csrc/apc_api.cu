@@ -59,61 +59,64 @@ void free_all(apc_ctx *c) {
         if (p) cudaFree(p);
 }
 
-// Pick cluster size, workers per warp, warps per CTA, ring depth and grid for
-// the iteration kernel.  Every CTA of a cluster gets W = ceil(m / cs) worker
-// slots; a stage holds R rows of W * P elements of Q.
-int configure(apc_ctx *c, int cs_request, int wpw_request) {
+// Pick cluster size, rows per pipeline step, workers per warp, warps per CTA,
+// ring depth and grid for the iteration kernel.  Every CTA of a cluster gets
+// W = ceil(m / cs) worker slots; a stage holds R rows of W * P elements of Q.
+int configure(apc_ctx *c, int cs_request, int wpw_request, int rg_request) {
     int dev_sms = 0;
     CK(c, cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, c->device));
     int smem_optin = 0;
     CK(c, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    const int R = kRowsPerGroup;
     const size_t qsz = q_elem_size(c->precision);
     const size_t budget = size_t(smem_optin) - 2 * 1024;
     // The smallest cluster whose CTAs hold at most 32 worker slots each: fewer
     // CTAs per row range means fewer cluster exchanges per row and more work
     // per pipeline step (sizes need not be powers of two; 8 is the portable
-    // maximum).
-    const int cands[8] = {1, 2, 3, 4, 5, 6, 7, 8};
-    for (int ci = 0; ci < 8; ++ci) {
-        const int cs = cands[ci];
+    // maximum).  At one cluster size two rows per step are preferred; one row
+    // per step halves the stages, which lets FP32 Q (twice the bytes of BF16)
+    // use the same cluster size as BF16 with a full ring.
+    for (int cs = 1; cs <= 8; ++cs) {
         if (cs_request > 0 && cs != cs_request) continue;
-        const int W0 = (c->m + cs - 1) / cs;
-        const int wpw = wpw_request > 0 ? wpw_request : (W0 >= 2 ? 2 : 1);
-        if (wpw < 1 || wpw > 2) continue;
-        const int nw = (W0 + wpw - 1) / wpw;
-        const int W = nw * wpw;  // worker slots per CTA
-        if (W > 32 || nw > kMaxElemWarps || (cs - 1) * W >= c->m) continue;
-        const size_t stage = size_t(R) * W * c->P * qsz;
-        // clusters that fit with the smallest ring, then the deepest ring that fits
-        int64_t clusters = std::min<int64_t>(std::max(1, dev_sms / cs), (c->n + R - 1) / R);
-        int stages = 0;
-        size_t smem = 0;
-        bool ok = false;
-        for (int pass = 0; pass < 4 && !ok; ++pass) {
-            const int64_t rpc = (c->n + clusters - 1) / clusters;
-            const size_t fixed = iter_smem_bytes(c->precision, c->P, W, 0, rpc);
-            if (fixed + size_t(kMinStages) * stage > budget) break;
-            stages = int(std::min<size_t>(6, (budget - fixed) / stage));
-            smem = iter_smem_bytes(c->precision, c->P, W, stages, rpc);
-            const int maxc = iter_max_clusters(c->precision, c->cpl, wpw, cs, nw, smem);
-            if (maxc <= 0) break;
-            if (maxc >= clusters) ok = true;
-            else clusters = maxc;
+        for (int R = kMaxRowsPerGroup; R >= 1; --R) {
+            if (rg_request > 0 && R != rg_request) continue;
+            const int W0 = (c->m + cs - 1) / cs;
+            const int wpw = wpw_request > 0 ? wpw_request : (W0 >= 2 ? 2 : 1);
+            if (wpw < 1 || wpw > 2) continue;
+            const int nw = (W0 + wpw - 1) / wpw;
+            const int W = nw * wpw;  // worker slots per CTA
+            if (W > 32 || nw > kMaxElemWarps || (cs - 1) * W >= c->m) continue;
+            const size_t stage = size_t(R) * W * c->P * qsz;
+            // clusters that fit with the smallest ring, then the deepest ring that fits
+            int64_t clusters = std::min<int64_t>(std::max(1, dev_sms / cs), (c->n + R - 1) / R);
+            int stages = 0;
+            size_t smem = 0;
+            bool ok = false;
+            for (int pass = 0; pass < 4 && !ok; ++pass) {
+                const int64_t rpc = (c->n + clusters - 1) / clusters;
+                const size_t fixed = iter_smem_bytes(c->precision, c->P, W, 0, rpc, R);
+                if (fixed + size_t(kMinStages) * stage > budget) break;
+                stages = int(std::min<size_t>(6, (budget - fixed) / stage));
+                smem = iter_smem_bytes(c->precision, c->P, W, stages, rpc, R);
+                const int maxc = iter_max_clusters(c->precision, c->cpl, wpw, cs, nw, R, smem);
+                if (maxc <= 0) break;
+                if (maxc >= clusters) ok = true;
+                else clusters = maxc;
+            }
+            if (!ok) continue;
+            c->cs = cs;
+            c->rg = R;
+            c->wpw = wpw;
+            c->nw = nw;
+            c->stages = stages;
+            c->clusters = int(clusters);
+            c->rows_per_cluster = (c->n + clusters - 1) / clusters;
+            c->smem = smem;
+            return APC_OK;
         }
-        if (!ok) continue;
-        c->cs = cs;
-        c->wpw = wpw;
-        c->nw = nw;
-        c->stages = stages;
-        c->clusters = int(clusters);
-        c->rows_per_cluster = (c->n + clusters - 1) / clusters;
-        c->smem = smem;
-        return APC_OK;
     }
     return fail(c, APC_ERR_UNSUPPORTED,
-                "no launch configuration fits m=%d blocks of width %d, n=%lld (requested cs=%d wpw=%d)", c->m, c->P,
-                (long long)c->n, cs_request, wpw_request);
+                "no launch configuration fits m=%d blocks of width %d, n=%lld (requested cs=%d wpw=%d rows=%d)", c->m,
+                c->P, (long long)c->n, cs_request, wpw_request, rg_request);
 }
 
 int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
@@ -133,6 +136,7 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         a.cs = c->cs;
         a.nw = c->nw;
         a.wpw = c->wpw;
+        a.rg = c->rg;
         a.stages = c->stages;
         a.mode = mode;
         a.rows_per_cluster = c->rows_per_cluster;
@@ -280,6 +284,8 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     if (m < 1 || m > 256) return fail(nullptr, APC_ERR_UNSUPPORTED, "m=%d outside 1..256", m);
     const int precision = opt ? opt->precision : APC_F32;
     if (precision < APC_F64 || precision > APC_BF16) return fail(nullptr, APC_ERR_INVALID_ARG, "bad precision");
+    if (opt && (opt->rows_per_group < 0 || opt->rows_per_group > 2))
+        return fail(nullptr, APC_ERR_INVALID_ARG, "rows_per_group=%d: 0 (automatic), 1 or 2", opt->rows_per_group);
     if (row_offsets_host[0] != 0 || row_offsets_host[m] != N)
         return fail(nullptr, APC_ERR_INVALID_ARG, "row_offsets must start at 0 and end at N");
     int64_t pmax = 0;
@@ -423,7 +429,9 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     CKB(cudaMemsetAsync(c->xbar, 0, sizeof(double) * n, s));
     CKB(cudaMemsetAsync(c->zbuf, 0, ssz * 3 * m * P, s));
     CKB(cudaMemsetAsync(c->err, 0, sizeof(int) * 4, s));
-    if ((rc = configure(c, opt ? opt->cluster_size : 0, opt ? opt->workers_per_warp : 0)) != APC_OK) return bail(rc);
+    if ((rc = configure(c, opt ? opt->cluster_size : 0, opt ? opt->workers_per_warp : 0,
+                        opt ? opt->rows_per_group : 0)) != APC_OK)
+        return bail(rc);
     CKB(cudaStreamSynchronize(s));
     *out = c;
     return APC_OK;
@@ -620,7 +628,7 @@ int apc_set_test_hooks(apc_ctx *c, int32_t grid_barrier_skew, double timeout_s) 
 }
 
 int apc_context_info(const apc_ctx *c, int64_t *n, int64_t *N, int32_t *m, int32_t *width, int32_t *cluster_size,
-                     int32_t *clusters, int64_t *q_bytes) {
+                     int32_t *clusters, int64_t *q_bytes, int32_t *rows_per_group) {
     if (!c) return APC_ERR_INVALID_ARG;
     if (n) *n = c->n;
     if (N) *N = c->N;
@@ -629,6 +637,7 @@ int apc_context_info(const apc_ctx *c, int64_t *n, int64_t *N, int32_t *m, int32
     if (cluster_size) *cluster_size = c->cs;
     if (clusters) *clusters = c->clusters;
     if (q_bytes) *q_bytes = int64_t(c->q_bytes);
+    if (rows_per_group) *rows_per_group = c->rg;
     return APC_OK;
 }
 

@@ -21,7 +21,7 @@ struct apc_ctx {
     uint32_t *bar = nullptr;
     int *err = nullptr;
     double *sums = nullptr, *xtmp = nullptr, *rtmp = nullptr, *xacc = nullptr, *rhs = nullptr;
-    int cs = 1, nw = 1, wpw = 1, stages = 2, clusters = 1;
+    int cs = 1, nw = 1, wpw = 1, rg = 2, stages = 2, clusters = 1;
     int64_t rows_per_cluster = 1;
     size_t smem = 0;
     int64_t t = 0;   // global pass counter (z buffer rotation)

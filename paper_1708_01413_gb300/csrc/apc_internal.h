@@ -28,6 +28,7 @@ struct IterArgs {
     int32_t cs;         // cluster size (CTAs sharing a row range)
     int32_t nw;         // warps per CTA
     int32_t wpw;        // workers per warp (1 or 2); worker slots per CTA = nw * wpw
+    int32_t rg;         // rows of Q per pipeline step (1 or 2); 2 * rg control warps
     int32_t stages;     // TMA ring depth
     int32_t mode;
     int64_t rows_per_cluster;
@@ -48,21 +49,22 @@ enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT_TMA = 1, DEV_TIMEOUT_XCHG = 2, DEV_T
 cudaError_t launch_iter(int precision, int cpl, const IterArgs &a, int clusters, size_t smem,
                         cudaStream_t s);
 // Maximum number of co-resident clusters for a configuration (0 on failure).
-int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t smem);
+int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, int rg, size_t smem);
 // Minimum ring depth: four stages are in use at a time.
 constexpr int kMinStages = 5;
 // Dynamic shared memory of one CTA: `slots` worker slots, `stages` ring stages.
-size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster);
-constexpr int kRowsPerGroup = 2;   // rows of Q per pipeline step
+size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster, int rg);
+constexpr int kMaxRowsPerGroup = 2;  // rows of Q per pipeline step: 1 or 2
 constexpr int kMaxElemWarps = 16;  // warps streaming Q per CTA of the iteration kernel
-constexpr int kCtlWarps = 4;       // control warps per CTA: per row of a group, one for the
-                                   // master's update and one for the machines' update
+constexpr int kCtlWarps = 2 * kMaxRowsPerGroup;  // control warps per CTA (at most): per row of
+                                   // a group, one for the master's update and one for the
+                                   // machines' update
 constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps) * 32;
 
 // Kernel entry points, one translation unit per Q precision.
-void *iter_kernel_f64(int cpl, int wpw, bool apc);
-void *iter_kernel_f32(int cpl, int wpw, bool apc);
-void *iter_kernel_bf16(int cpl, int wpw, bool apc);
+void *iter_kernel_f64(int cpl, int wpw, bool apc, int rg);
+void *iter_kernel_f32(int cpl, int wpw, bool apc, int rg);
+void *iter_kernel_bf16(int cpl, int wpw, bool apc, int rg);
 
 // ---- setup (FP64) -----------------------------------------------------------
 cudaError_t launch_rownorm(const double *A, int64_t lda, int64_t N, int64_t n, double *dinv, int *err,

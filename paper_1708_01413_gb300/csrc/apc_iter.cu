@@ -6,11 +6,11 @@ namespace apc {
 
 namespace {
 
-void *kernel_for(int precision, int cpl, int wpw, bool apc = true) {
+void *kernel_for(int precision, int cpl, int wpw, bool apc, int rg) {
     switch (precision) {
-        case 0: return iter_kernel_f64(cpl, wpw, apc);
-        case 1: return iter_kernel_f32(cpl, wpw, apc);
-        case 2: return iter_kernel_bf16(cpl, wpw, apc);
+        case 0: return iter_kernel_f64(cpl, wpw, apc, rg);
+        case 1: return iter_kernel_f32(cpl, wpw, apc, rg);
+        case 2: return iter_kernel_bf16(cpl, wpw, apc, rg);
         default: return nullptr;
     }
 }
@@ -18,10 +18,11 @@ void *kernel_for(int precision, int cpl, int wpw, bool apc = true) {
 size_t q_size(int precision) { return precision == 0 ? 8 : precision == 1 ? 4 : 2; }
 size_t s_size(int precision) { return precision == 0 ? 8 : 4; }
 
-cudaLaunchConfig_t make_config(int cs, int nw, int clusters, size_t smem, cudaStream_t s, cudaLaunchAttribute *attr) {
+cudaLaunchConfig_t make_config(int cs, int nw, int rg, int clusters, size_t smem, cudaStream_t s,
+                               cudaLaunchAttribute *attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(clusters * cs), 1, 1);
-    cfg.blockDim = dim3(unsigned((nw + kCtlWarps) * 32), 1, 1);
+    cfg.blockDim = dim3(unsigned((nw + 2 * rg) * 32), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -35,13 +36,13 @@ cudaLaunchConfig_t make_config(int cs, int nw, int clusters, size_t smem, cudaSt
 
 }  // namespace
 
-size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster) {
-    return iterk::SmemLayout(q_size(precision), s_size(precision), slots, P, stages, rows_per_cluster).total;
+size_t iter_smem_bytes(int precision, int P, int slots, int stages, int64_t rows_per_cluster, int rg) {
+    return iterk::SmemLayout(q_size(precision), s_size(precision), slots, P, stages, rows_per_cluster, rg).total;
 }
 
-int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t smem) {
-    void *k = kernel_for(precision, cpl, wpw, true);
-    void *k2 = kernel_for(precision, cpl, wpw, false);
+int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, int rg, size_t smem) {
+    void *k = kernel_for(precision, cpl, wpw, true, rg);
+    void *k2 = kernel_for(precision, cpl, wpw, false, rg);
     if (!k || !k2) return 0;
     if (cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) {
         cudaGetLastError();
@@ -52,7 +53,7 @@ int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t sm
         return 0;
     }
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = make_config(cs, nw, 1, smem, nullptr, attr);
+    cudaLaunchConfig_t cfg = make_config(cs, nw, rg, 1, smem, nullptr, attr);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
@@ -62,12 +63,12 @@ int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, size_t sm
 }
 
 cudaError_t launch_iter(int precision, int cpl, const IterArgs &a, int clusters, size_t smem, cudaStream_t s) {
-    void *k = kernel_for(precision, cpl, a.wpw, a.mode == MODE_APC);
+    void *k = kernel_for(precision, cpl, a.wpw, a.mode == MODE_APC, a.rg);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;
     cudaLaunchAttribute attr[1];
-    cudaLaunchConfig_t cfg = make_config(a.cs, a.nw, clusters, smem, s, attr);
+    cudaLaunchConfig_t cfg = make_config(a.cs, a.nw, a.rg, clusters, smem, s, attr);
     void *args[] = {const_cast<IterArgs *>(&a)};
     return cudaLaunchKernelExC(&cfg, k, args);
 }

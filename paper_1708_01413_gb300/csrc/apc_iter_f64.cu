@@ -2,5 +2,7 @@
 #include "apc_iter_impl.cuh"
 
 namespace apc {
-void *iter_kernel_f64(int cpl, int wpw, bool apc) { return iterk::kernel_for<double, double>(cpl, wpw, apc); }
+void *iter_kernel_f64(int cpl, int wpw, bool apc, int rg) {
+    return iterk::kernel_for<double, double>(cpl, wpw, apc, rg);
+}
 }  // namespace apc

@@ -18,13 +18,15 @@
 // shared memory, completing on their mbarriers).  Partial z_i' of all clusters
 // are summed with global atomics, then one grid-wide barrier per iteration.
 //
-// Pipeline.  Rows go in groups of R = 2; one __syncthreads per step.  Element
-// warps stream Q: step t computes the first product of group t and the second
-// product of group t-3.  Two control warps own one row of a group each, one
-// lane per worker slot: after the barrier of step t they finish the master's
-// update of group t-2 (its cluster exchange was sent two steps earlier) and
-// write the second product's coefficients, then apply the machines' updates
-// of group t, form the CTA row sum and send it to the cluster.  Q rows stream
+// Pipeline.  Rows go in groups of R = 2 (or R = 1 where two rows of Q per
+// stage would not leave a deep enough ring); one __syncthreads per step.
+// Element warps stream Q: step t computes the first product of group t and
+// the second product of group t-3.  Each row of a group has two control warps,
+// one lane per worker slot: after the barrier of step t one finishes the
+// master's update of group t-2 (its cluster exchange was sent two steps
+// earlier) and writes the second product's coefficients, the other applies
+// the machines' updates of group t, forms the CTA row sum and sends it to the
+// cluster.  Q rows stream
 // into a ring of S shared-memory stages through TMA bulk copies (L2
 // evict-first); four stages are in use, S-4 are loading.
 //
@@ -52,8 +54,6 @@
 namespace apc {
 namespace iterk {
 
-constexpr int R = kRowsPerGroup;   // rows per group (= 2, hard-wired below)
-static_assert(R == 2, "the transposed butterfly and lane roles assume 2 rows per group");
 // Cluster exchange buffers (groups in flight).  A peer writes group g + NX's
 // row sums into the slot of group g only after its master has seen this CTA's
 // sums of group g + NX - 2, which this CTA's update warps send in step
@@ -67,7 +67,8 @@ __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + 
 
 struct SmemLayout {
     size_t stage_elems, row_stride, off_xb, off_d, off_coef, off_sloc, off_xh, off_bars, total;
-    __host__ __device__ SmemLayout(size_t q_elem, size_t s_elem, int slots, int P, int stages, int64_t rpc) {
+    // R = rows per group (1 or 2)
+    __host__ __device__ SmemLayout(size_t q_elem, size_t s_elem, int slots, int P, int stages, int64_t rpc, int R) {
         row_stride = size_t(slots) * P;               // elements per staged row
         stage_elems = size_t(R) * row_stride;
         // xbar [2][rpc], 8 bytes per row: FP64, or an FP32 hi/lo pair on the
@@ -243,8 +244,9 @@ __device__ __forceinline__ float2 df_from(double v) {
     return make_float2(hi, float(v - double(hi)));
 }
 
-template <typename TQ, typename TS, int CPL, int WPW, bool kAPC>
+template <typename TQ, typename TS, int CPL, int WPW, bool kAPC, int R>
 __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs a) {
+    static_assert(R == 1 || R == 2, "one or two rows per group");
     using TC = TS;
     constexpr bool kF64 = sizeof(TS) == 8;
     constexpr bool kDF = kAPC && !kF64;     // master update in double-float
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     const int P = a.P, nwe = a.nw, S = a.stages, m = a.m, cs = a.cs;
     const int W = nwe * WPW;  // worker slots per CTA (<= 32)
     const int rpc = int(a.rows_per_cluster);
-    const SmemLayout L(sizeof(TQ), sizeof(TS), W, P, S, rpc);
+    const SmemLayout L(sizeof(TQ), sizeof(TS), W, P, S, rpc, R);
     TQ *stage_base = reinterpret_cast<TQ *>(smem);
     double *xbd = reinterpret_cast<double *>(smem + L.off_xb);  // [2][rpc] FP64 xbar
     float2 *xbf = reinterpret_cast<float2 *>(smem + L.off_xb);  // [2][rpc] double-float xbar (same bytes)
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     uint64_t *xchg = full + S;                                          // [NX]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // Warps [0, nwe) stream Q (both products).  Four control warps own the
+    // Warps [0, nwe) stream Q (both products).  2R control warps own the
     // rows of a group; lane s handles worker slot s.  Control warp r (r < R)
     // runs the master's update of row r of group t-2 and the second product's
     // coefficients; control warp R + r runs the machines' updates of row r of
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
     // of control warp 1 issues TMA.
     const bool is_ctl = warp >= nwe;
     const int ctl_r = warp - nwe;
-    const int ctl_row = ctl_r & 1;
+    const int ctl_row = R == 2 ? (ctl_r & 1) : 0;
     const bool ctl_master = is_ctl && ctl_r < R;
     const int issuer = (nwe + 1) * 32;
     const uint32_t rank = cluster_rank();
@@ -379,13 +381,13 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 qoff[sl][r][h] = uint32_t((r * L.row_stride + (warp * WPW + sl) * P + (h * 32 + lane) * V) * sizeof(TQ));
     const uint32_t stage_bytes = uint32_t(L.stage_elems * sizeof(TQ));
     // element lane (r_l, s_l) publishes w_i of row r_l of worker slot warp*WPW + s_l
-    const int r_l = lane >> 4, s_l = lane & 15;
-    const bool d_lane = !is_ctl && s_l < WPW;
+    const int r_l = R == 2 ? lane >> 4 : 0, s_l = lane & 15;
+    const bool d_lane = !is_ctl && s_l < WPW && (R == 2 || lane < 16);
     const int wl_d = warp * WPW + s_l;
 
     // ---- control warps: x_i of (row ctl_r, slot lane), one group ahead ----
     const bool c_act = is_ctl && lane < W_cta;
-    TS *const cx0 = xw + size_t(row0 + (ctl_r & 1)) * m + lane;
+    TS *const cx0 = xw + size_t(row0 + ctl_row) * m + lane;
     const size_t xstep = size_t(R) * m;
     const bool cx_ok = rx && c_act && !ctl_master;
     TS *cx_next = cx0;
@@ -437,10 +439,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                         }
                         dr[r] = d0 + d1;
                     }
-                    // transposed butterfly: lanes 0-15 end with row 0, lanes 16-31 with row 1
-                    TC keep = (lane & 16) ? dr[1] : dr[0];
-                    const TC send = (lane & 16) ? dr[0] : dr[1];
-                    keep += __shfl_xor_sync(0xffffffffu, send, 16);
+                    TC keep;
+                    if constexpr (R == 2) {
+                        // transposed butterfly: lanes 0-15 end with row 0, lanes 16-31 with row 1
+                        keep = (lane & 16) ? dr[1] : dr[0];
+                        const TC send = (lane & 16) ? dr[0] : dr[1];
+                        keep += __shfl_xor_sync(0xffffffffu, send, 16);
+                    } else {
+                        keep = dr[0] + __shfl_xor_sync(0xffffffffu, dr[0], 16);
+                    }
 #pragma unroll
                     for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
                     dsum[sl] = keep;
@@ -680,10 +687,10 @@ abort_exit:
     cluster_sync_all();
 }
 
-template <typename TQ, typename TS>
-void *kernel_for(int cpl, int wpw, bool apc) {
-#define APC_K(C, WP) (apc ? reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, true>) \
-                          : reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, false>))
+template <typename TQ, typename TS, int RG>
+void *kernel_for_rg(int cpl, int wpw, bool apc) {
+#define APC_K(C, WP) (apc ? reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, true, RG>) \
+                          : reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, false, RG>))
     if (wpw == 1) {
         switch (cpl) {
             case 2: return APC_K(2, 1);
@@ -699,6 +706,11 @@ void *kernel_for(int cpl, int wpw, bool apc) {
     }
 #undef APC_K
     return nullptr;
+}
+
+template <typename TQ, typename TS>
+void *kernel_for(int cpl, int wpw, bool apc, int rg) {
+    return rg == 1 ? kernel_for_rg<TQ, TS, 1>(cpl, wpw, apc) : rg == 2 ? kernel_for_rg<TQ, TS, 2>(cpl, wpw, apc) : nullptr;
 }
 
 }  // namespace iterk

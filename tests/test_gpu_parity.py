@@ -182,6 +182,38 @@ def test_cluster_sizes_not_powers_of_two(cs, m):
     assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= 1e-10
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 1e-5)])
+@pytest.mark.parametrize("rg,cs", [(1, 0), (1, 2), (1, 4), (2, 0), (2, 4)])
+def test_rows_per_group_agree(prec, tol, rg, cs):
+    # one or two rows of Q per pipeline step (2 or 4 control warps, a full or a
+    # transposed butterfly for the first product) give the oracle's trajectory
+    apc, dev = _apc(), _dev()
+    n, m, T = 1201, 16, 30
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 7)
+    ref = O.apc_run(A, b, offs, g, e, max_iters=T, Qs=Qs, Rs=Rs)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec,
+                        cluster_size=cs, rows_per_group=rg)
+    info = ctx.info()
+    assert info["rows_per_group"] == rg and (cs == 0 or info["cluster_size"] == cs)
+    ctx.reset()
+    ctx.iterate(g, e, T)
+    assert _rel(ctx.xbar().cpu().numpy(), ref.xbar) <= tol
+
+
+@pytest.mark.parametrize("prec,n,m,want", [("bf16", 16640, 128, (4, 2)), ("f32", 16640, 128, (4, 1)),
+                                           ("f32", 8192, 32, (1, 1)), ("bf16", 8192, 32, (1, 2))])
+def test_automatic_configuration(prec, n, m, want):
+    # blocks of 130 / 256 rows (width 256): the smallest cluster whose CTAs hold
+    # <= 32 workers, two rows per step where the ring still has >= 5 stages of
+    # two rows (BF16), one row otherwise (FP32 stages are twice as large)
+    apc, dev = _apc(), _dev()
+    A, _, b = inputs.gaussian_system_torch(n, 3, dev)
+    ctx = apc.apc_setup(A, b, inputs.even_offsets(n, m), precision=prec)
+    info = ctx.info()
+    assert (info["cluster_size"], info["rows_per_group"]) == want, info
+    assert info["width"] == 256
+
+
 def test_bf16_trajectory_close_to_oracle():
     apc, dev = _apc(), _dev()
     n, m, T = 2048, 8, 20
@@ -240,6 +272,9 @@ def test_errors_reported():
     assert ei.value.name == "NONFINITE"
     with pytest.raises(apc.ApcError) as ei:
         apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), [0, 10, 10, 64])
+    assert ei.value.name == "INVALID_ARG"
+    with pytest.raises(apc.ApcError) as ei:
+        apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, rows_per_group=3)
     assert ei.value.name == "INVALID_ARG"
     ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f32")
     ctx.reset()
