@@ -332,8 +332,11 @@ def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
         s32 = a0.elapsed_time(a1) / 1e3
         b32 = c32.info()["q_bytes"] + 2 * m * n * 4 + 2 * n * 8
         gbs = b32 * 3 * T / s32 / 1e9
+        info = c32.info()
+        tpi = measured_traffic(f"n={n},m={m},f32")
         return {"iter_per_s": 3 * T / s32, "hbm_gbs": gbs, "frac": gbs / peak,
-                "cluster_size": c32.info()["cluster_size"]}
+                "cluster_size": info["cluster_size"], "rows_per_group": info["rows_per_group"],
+                "algorithmic_bytes_per_iter": b32, "traffic_bytes_per_iter": tpi}
     finally:
         c32.close()
 
