@@ -36,7 +36,8 @@
 // copies, issued by a producer warp into a ring of 4 basis slots and 2 x_i
 // slots; 8 consumer warps wait on the slots' mbarriers (bounded waits) and
 // release them with per-warp arrivals, so no CTA-wide barrier sits in the
-// streaming loop.  Units are assigned to CTAs on the host, longest first.
+// streaming loop.  The CTAs claim units at run time from one counter per
+// sweep, longest units first.
 //
 // Precision: Q_i is BF16 (rounded once from the FP64 QR); products accumulate
 // in FP32 on the tensor cores; an operand split into planes keeps 16 (sweep
@@ -72,6 +73,7 @@ constexpr int kWin = 64;         // basis columns per sweep-A window (one 128-by
 constexpr int kColsB = 512;      // columns of a sweep-B unit (64 per consumer warp)
 constexpr int kRowsStageB = 32;  // rows per sweep-B stage
 constexpr int kQSlots = 4, kXSlots = 2;
+constexpr int kUQ = 4;           // depth of the queue of claimed units (producer -> consumers)
 constexpr int kPlanesA = 2, kPlanesB = 3;
 constexpr int kSlotQBytes = kTileRows * kWin * 2;  // 32 KB: 256 x 64 or 8 x (32 x 64) BF16
 constexpr int kSlotZBytes = 8192;                  // operand planes of one stage
@@ -79,7 +81,8 @@ constexpr int kSlotBytes = kSlotQBytes + kSlotZBytes;
 constexpr int kXPad = 8;                           // FP32 padding per right-hand-side row of an x_i tile
 constexpr int kXSlotBytes = 32 * (kTileRows + kXPad) * 4;
 constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
-constexpr size_t kSmemBytes = size_t(kBarOffset) + 2 * (kQSlots + kXSlots) * sizeof(uint64_t);
+// mbarriers: Q slots full/empty, x slots full/empty, unit queue full/empty; then the queue
+constexpr size_t kSmemBytes = size_t(kBarOffset) + 2 * (kQSlots + kXSlots + kUQ) * sizeof(uint64_t) + kUQ * sizeof(int);
 
 struct SysDesc {
     const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
@@ -97,10 +100,10 @@ struct SysDesc {
 
 struct BatchArgs {
     const SysDesc *sys;
-    const int2 *unitsA;  // (system, first row of the tile)
-    const int *offA;     // [grid + 1]
-    const int2 *unitsB;  // (system, first column)
-    const int *offB;     // [grid + 1]
+    const int2 *unitsA;  // (system, first row of the tile), longest first
+    const int2 *unitsB;  // (system, first column), longest first
+    int nA, nB;
+    uint32_t *ctr;       // [3] claim counters, one per sweep, rotating (zero at launch)
     int64_t iters;
     int init;
     int hb;              // 1: distributed-preconditioned heavy ball instead of APC
@@ -597,6 +600,9 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
     Ring R{smem, bars, bars + kQSlots, bars + 2 * kQSlots, bars + 2 * kQSlots + kXSlots, &abort_flag,
            a.timeout_ns};
+    uint64_t *uqfull = bars + 2 * kQSlots + 2 * kXSlots;  // [kUQ] a claimed unit is in the queue
+    uint64_t *uqempty = uqfull + kUQ;                     // [kUQ] every consumer warp has read it
+    volatile int *uq = reinterpret_cast<volatile int *>(uqempty + kUQ);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == kConsumerWarps;
     if (threadIdx.x == 0) {
@@ -609,18 +615,69 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
             mbar_init(&R.xfull[s], 1);
             mbar_init(&R.xempty[s], kConsumerWarps);
         }
+        for (int s = 0; s < kUQ; ++s) {
+            mbar_init(&uqfull[s], 1);
+            mbar_init(&uqempty[s], kConsumerWarps);
+        }
         fence_mbar_init_cluster();
     }
     __syncthreads();
     const uint64_t policy = policy_evict_first();
     Cursor cur;
+    uint32_t uk = 0;  // units handed over so far (same count in the producer and every consumer warp)
     uint32_t episode = 0;
     bool ok = true;
+
+    // One sweep.  The CTAs claim units from a global counter (the lists are
+    // sorted longest first, so this is list scheduling with the longest units
+    // first and the imbalance at the grid barrier is at most the shortest
+    // units).  The producer claims ahead of the consumers and hands each unit
+    // over through a small queue, so the ring keeps streaming across unit
+    // boundaries; a claim past the end hands over -1 and ends the sweep.
+    auto sweep = [&](bool is_a, uint32_t e, bool init, bool hb) {
+        const int nunits = is_a ? a.nA : a.nB;
+        const int2 *units = is_a ? a.unitsA : a.unitsB;
+        // the counter of two sweeps ago: every claim on it ended before the last grid barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr[(e + 1) % 3] = 0u;
+        if (producer) {
+            if (lane != 0) return;
+            for (;;) {
+                const int s = int(uk % kUQ);
+                int u = -1;
+                if (uk < uint32_t(kUQ) || R.wait(&uqempty[s], ((uk / kUQ) - 1) & 1)) {
+                    u = int(atomicAdd(&a.ctr[e % 3], 1u));
+                    if (u >= nunits) u = -1;
+                }
+                uq[s] = u;
+                mbar_arrive(&uqfull[s]);
+                ++uk;
+                if (u < 0) return;
+                const int2 U = units[u];
+                if (is_a) sweep_a_producer<MT>(R, cur, a.sys[U.x], U.y, init || hb, policy);
+                else sweep_b_producer<MT>(R, cur, a.sys[U.x], U.y, policy);
+            }
+        } else {
+            for (;;) {
+                const int s = int(uk % kUQ);
+                if (!R.wait(&uqfull[s], (uk / kUQ) & 1)) return;
+                const int u = uq[s];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&uqempty[s]);
+                ++uk;
+                if (u < 0) return;
+                const int2 U = units[u];
+                const SysDesc &d = a.sys[U.x];
+                if (is_a) sweep_a_consumer<MT>(R, cur, d, U.y, init, hb, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
+                else sweep_b_consumer<MT>(R, cur, d, U.y);
+            }
+        }
+    };
+
     if (a.init) {
         // z_i(0) = -c_i, so that sweep A with gamma = 1 and x = xbar = 0 forms
         // the least-norm x_i(0) = Q_i c_i (Algorithm 1) and xbar(0) their mean
         if (!producer)
-            for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1]; ++u) {
+            for (int u = blockIdx.x; u < a.nB; u += gridDim.x) {
                 const int2 U = a.unitsB[u];
                 const SysDesc &d = a.sys[U.x];
                 if (64 * warp < min(kColsB, d.Cq - U.y)) {
@@ -633,27 +690,10 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     }
     for (int64_t it = 0; ok && it < a.iters; ++it) {
         const bool init = a.init && it == 0;
-        for (int u = a.offA[blockIdx.x]; u < a.offA[blockIdx.x + 1] && !R.aborted(); ++u) {
-            const int2 U = a.unitsA[u];
-            const SysDesc &d = a.sys[U.x];
-            const bool hb = a.hb && !init;
-            if (producer) {
-                if (lane == 0) sweep_a_producer<MT>(R, cur, d, U.y, init || hb, policy);
-            } else {
-                sweep_a_consumer<MT>(R, cur, d, U.y, init, hb, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
-            }
-        }
+        sweep(true, episode, init, a.hb && !init);
         ++episode;
         if (!(ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag))) break;
-        for (int u = a.offB[blockIdx.x]; u < a.offB[blockIdx.x + 1] && !R.aborted(); ++u) {
-            const int2 U = a.unitsB[u];
-            const SysDesc &d = a.sys[U.x];
-            if (producer) {
-                if (lane == 0) sweep_b_producer<MT>(R, cur, d, U.y, policy);
-            } else {
-                sweep_b_consumer<MT>(R, cur, d, U.y);
-            }
-        }
+        sweep(false, episode, false, false);
         if (it + 1 < a.iters) {
             ++episode;
             ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
@@ -764,8 +804,7 @@ struct apc_batch {
     std::vector<void *> owned;
     SysDesc *d_desc = nullptr;
     int2 *d_unitsA = nullptr, *d_unitsB = nullptr;
-    int *d_offA = nullptr, *d_offB = nullptr;
-    uint32_t *bar = nullptr;
+    uint32_t *bar = nullptr;  // [4]: grid barrier counter, then the three claim counters
     int *err = nullptr;
     bool reset_done = false, params_set = false;
     int method = 0;  // 0: APC, 1: heavy ball (apc_batch_set_hb_params)
@@ -813,36 +852,25 @@ const void *kernel_ptr(int MT) {
                    : reinterpret_cast<const void *>(&apc_batch_kernel<2>);
 }
 
-// Longest-processing-time assignment of units to CTAs, as CSR lists.
-void lpt(std::vector<std::pair<double, int2>> items, int bins, std::vector<int2> &units, std::vector<int> &off) {
+// Units sorted longest first (by bytes streamed); the CTAs claim them in this
+// order at run time.
+std::vector<int2> longest_first(std::vector<std::pair<double, int2>> items) {
     std::stable_sort(items.begin(), items.end(),
                      [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
-    std::vector<std::vector<int2>> per(bins);
-    using P = std::pair<double, int>;
-    std::priority_queue<P, std::vector<P>, std::greater<P>> heap;
-    for (int i = 0; i < bins; ++i) heap.push({0.0, i});
-    for (const auto &it : items) {
-        P top = heap.top();
-        heap.pop();
-        per[top.second].push_back(it.second);
-        heap.push({top.first + it.first, top.second});
-    }
-    units.clear();
-    off.assign(1, 0);
-    for (auto &v : per) {
-        std::sort(v.begin(), v.end(), [](int2 x, int2 y) { return x.x != y.x ? x.x < y.x : x.y < y.y; });
-        units.insert(units.end(), v.begin(), v.end());
-        off.push_back(int(units.size()));
-    }
+    std::vector<int2> units;
+    units.reserve(items.size());
+    for (const auto &it : items) units.push_back(it.second);
+    return units;
 }
 
 int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
     BatchArgs a = {};
     a.sys = b->d_desc;
     a.unitsA = b->d_unitsA;
-    a.offA = b->d_offA;
     a.unitsB = b->d_unitsB;
-    a.offB = b->d_offB;
+    a.nA = b->units_a;
+    a.nB = b->units_b;
+    a.ctr = b->bar + 1;
     a.iters = iters;
     a.init = init;
     a.hb = init ? 0 : b->method;
@@ -850,7 +878,7 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
     a.bar = b->bar;
     a.err = b->err;
     a.timeout_ns = uint64_t(b->timeout_s * 1e9);
-    BCK(b, cudaMemsetAsync(b->bar, 0, sizeof(uint32_t), s));
+    BCK(b, cudaMemsetAsync(b->bar, 0, sizeof(uint32_t) * 4, s));
     if (b->MT == 1)
         apc_batch_kernel<1><<<b->grid, kThreads, kSmemBytes, s>>>(a);
     else
@@ -1053,21 +1081,14 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             ib.push_back({double(d.npad) * (2.0 * cols + 32.0), make_int2(sys, c0)});
         }
     }
-    std::vector<int2> ua, ub;
-    std::vector<int> oa, ob;
-    lpt(ia, b->grid, ua, oa);
-    lpt(ib, b->grid, ub, ob);
+    const std::vector<int2> ua = longest_first(ia), ub = longest_first(ib);
     b->units_a = int(ua.size());
     b->units_b = int(ub.size());
     if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * ua.size())) ||
-        (rc = balloc(b, &b->d_offA, sizeof(int) * oa.size())) ||
-        (rc = balloc(b, &b->d_unitsB, sizeof(int2) * ub.size())) ||
-        (rc = balloc(b, &b->d_offB, sizeof(int) * ob.size())))
+        (rc = balloc(b, &b->d_unitsB, sizeof(int2) * ub.size())))
         return bail(rc);
     cudaMemcpyAsync(b->d_unitsA, ua.data(), sizeof(int2) * ua.size(), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->d_offA, oa.data(), sizeof(int) * oa.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->d_unitsB, ub.data(), sizeof(int2) * ub.size(), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->d_offB, ob.data(), sizeof(int) * ob.size(), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         bfail(b, APC_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
