@@ -12,35 +12,41 @@
 // z_i does not depend on x_i, so the second product is one GEMM per system,
 // Y = Q^T xbar, over the packed basis Q = [Q_1 .. Q_m] (n x C).
 //
-// One iteration is two sweeps separated by grid barriers:
-//   sweep A  unit = (system, tile of 256 rows); a consumer warp owns 32 rows.
-//            The packed columns are walked in 64-column windows; for every
-//            16-column chunk of machine i, W^T += Z_i^T Q_i^T (mma.sync
-//            m16n8k16; A = z_i split into two BF16 planes, B = the basis via
-//            ldmatrix), and after the machine's last chunk its update and the
-//            running row sum; at the end of the unit the master's row update
-//            (double-float) and xbar' split into three BF16 planes, stored in
-//            the A-fragment order of sweep B.
-//   sweep B  unit = (system, 512 columns); a consumer warp owns 64 columns,
-//            all rows: Y^T = xbar'^T Q (A = the planes, B = the basis via
-//            ldmatrix.trans), then Z = Y - c split into two planes, stored in
-//            the A-fragment order of sweep A.
-// The accumulator fragment of one sweep is, lane for lane, the operand
-// fragment of the other, so no transposes are needed.
+// One iteration is two sweeps separated by grid barriers, both on the 5th
+// generation tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32
+// accumulators in tensor memory), issued by one thread of a tensor-core warp:
+//   sweep A  unit = (system, tile of 256 rows).  The packed columns are walked
+//            in 64-column windows; for every 16-column chunk of machine i,
+//            D += Q[rows, chunk] Z[chunk, 2 planes x k] (M = 128 rows per
+//            instruction, N = 2k; z_i split into two BF16 planes), into one
+//            of two accumulator buffers.  After the machine's last chunk the
+//            consumers (thread = row) read its w_i = Q_i z_i from tensor
+//            memory, update x_i and the running row sum while the tensor
+//            cores go on with the next machine in the other buffer; at the end
+//            of the unit the master's row update (double-float) and xbar'
+//            split into three BF16 planes.
+//   sweep B  unit = (system, 512 columns): D += Q[rows, cols]^T xbar'[rows,
+//            3 planes x k] over all rows (M = 128 columns per instruction, the
+//            basis read MN-major), then the consumers (thread = column) form
+//            Z = Y - c split into two planes for sweep A.
+// Operands: the basis windows are 128-byte swizzled K-major (sweep A) and
+// MN-major (sweep B) matrices as stored; the plane operands are K-major core
+// matrices (op_offset), written so by the other sweep's epilogue.
 //
 // Data movement.  The basis is stored tile-major and pre-swizzled: for each
 // 256-row tile and 64-column window a contiguous [rows][64] BF16 block whose
-// 16-byte chunks are XOR-permuted by (row & 7), the order ldmatrix reads
-// without bank conflicts.  A machine's x_i tile is likewise one contiguous
-// block ([k][rows + 8] FP32).  So every stage is one or a few 1-D TMA bulk
-// copies, issued by a producer warp into a ring of 4 basis slots and 2 x_i
-// slots; 8 consumer warps wait on the slots' mbarriers (bounded waits) and
-// release them with per-warp arrivals, so no CTA-wide barrier sits in the
-// streaming loop.  The CTAs claim units at run time from one counter per
-// sweep, longest units first.
+// 16-byte chunks are XOR-permuted by (row & 7), the 128-byte swizzle of the
+// tensor cores.  A machine's x_i tile is likewise one contiguous block ([k][rows]
+// FP32).  So every stage is one or a few 1-D TMA bulk copies, issued by a
+// producer warp into a ring of 4 basis slots and 2 x_i slots; the tensor-core
+// warp waits on the slots' mbarriers and releases them with tcgen05.commit,
+// the 8 consumer warps wait on the accumulators and x_i slots and release
+// them with per-warp arrivals (every wait bounded), so no CTA-wide barrier
+// sits in the streaming loop.  The CTAs claim units at run time from one
+// counter per sweep, longest units first.
 //
 // Precision: Q_i is BF16 (rounded once from the FP64 QR); products accumulate
-// in FP32 on the tensor cores; an operand split into planes keeps 16 (sweep
+// in FP32 in tensor memory; an operand split into planes keeps 16 (sweep
 // A) or 24 (sweep B) significant bits of its FP32 value.  z_i tends to zero
 // as the iteration converges, so its error is relative to the step; xbar does
 // not, hence the third plane there.
@@ -67,7 +73,9 @@ namespace {
 using namespace apc;
 
 constexpr int kConsumerWarps = 8;
-constexpr int kThreads = 32 * (kConsumerWarps + 1);  // + one producer warp
+constexpr int kProducerWarp = kConsumerWarps;       // issues the bulk copies
+constexpr int kMmaWarp = kConsumerWarps + 1;        // issues the tensor-core instructions
+constexpr int kThreads = 32 * (kConsumerWarps + 2);
 constexpr int kTileRows = 256;   // rows of a sweep-A unit (32 per consumer warp)
 constexpr int kWin = 64;         // basis columns per sweep-A window (one 128-byte row)
 constexpr int kColsB = 512;      // columns of a sweep-B unit (64 per consumer warp)
@@ -78,19 +86,24 @@ constexpr int kPlanesA = 2, kPlanesB = 3;
 constexpr int kSlotQBytes = kTileRows * kWin * 2;  // 32 KB: 256 x 64 or 8 x (32 x 64) BF16
 constexpr int kSlotZBytes = 8192;                  // operand planes of one stage
 constexpr int kSlotBytes = kSlotQBytes + kSlotZBytes;
-constexpr int kXPad = 8;                           // FP32 padding per right-hand-side row of an x_i tile
+constexpr int kXPad = 0;                           // FP32 padding per right-hand-side row of an x_i tile
 constexpr int kXSlotBytes = 32 * (kTileRows + kXPad) * 4;
 constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
-// mbarriers: Q slots full/empty, x slots full/empty, unit queue full/empty; then the queue
-constexpr size_t kSmemBytes = size_t(kBarOffset) + 2 * (kQSlots + kXSlots + kUQ) * sizeof(uint64_t) + kUQ * sizeof(int);
+// mbarriers: Q slots full/empty, x slots full/empty, unit queue full/empty,
+// sweep-A accumulators full/free (two buffers), sweep-B accumulator full/free,
+// drain; then the unit queue and the tensor-memory address
+constexpr int kNumBars = 2 * kQSlots + 2 * kXSlots + 2 * kUQ + 4 + 3;
+constexpr size_t kSmemUsed = size_t(kBarOffset) + kNumBars * sizeof(uint64_t) + (kUQ + 1) * sizeof(int);
+constexpr size_t kSmemBytes = kSmemUsed + 1024;     // slack to align the slots to 1024 bytes
+constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, sweep B: 4 x 3k
 
 struct SysDesc {
     const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
     float *X;                // tile-major x_i blocks (see x_block)
     float2 *Xb;              // [kp][npad]  master estimate, double-float
-    uint4 *Xfrag;            // [npad/16][MT][kPlanesB][32]  xbar' operand planes
-    uint2 *Zfrag;            // [Cq/8][MT][kPlanesA][32]     z operand planes
-    const float4 *Cfrag;     // [Cq/8][MT][32]               c_i, FP32
+    uint8_t *Xop;            // xbar' planes, B operand of sweep B (see op_offset), npad x 3kp BF16
+    uint8_t *Zop;            // z planes, B operand of sweep A (see op_offset), Cq x 2kp BF16
+    const float *Ct;         // [kp][Cq] c_i, FP32
     const int *coloff;       // [m + 1], multiples of 16
     float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float
     int npad, m, Cq, C;
@@ -125,30 +138,59 @@ __host__ __device__ __forceinline__ size_t x_block(int m, int kp, int npad, int 
 }
 
 // ---- PTX wrappers ------------------------------------------------------------
-__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+__device__ __forceinline__ float lds_f32(uint32_t addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
 }
-__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(addr));
+// Byte offset of element (n, kk) of a B operand stored as K-major core
+// matrices without swizzle: for every 16 values of kk a block of `nrows` x 16
+// BF16, made of 8 x 8 core matrices (n-group n/8 at 256 bytes, k-group at 128
+// bytes, 16 bytes per row).  In the descriptor: leading-dimension offset 128
+// (between k-groups), stride-dimension offset 256 (between n-groups).
+__host__ __device__ __forceinline__ size_t op_offset(int nrows, int n, int64_t kk) {
+    return size_t(kk >> 4) * nrows * 32 + size_t(n >> 3) * 256 + size_t((kk >> 3) & 1) * 128 + size_t(n & 7) * 16 +
+           size_t(kk & 7) * 2;
 }
-__device__ __forceinline__ void lds64(uint32_t addr, uint32_t &x, uint32_t &y) {
-    asm volatile("ld.shared.v2.u32 {%0,%1}, [%2];" : "=r"(x), "=r"(y) : "r"(addr));
+
+// ---- tensor cores (tcgen05): operands in shared memory, accumulators in tensor memory ----
+// Shared-memory matrix descriptor: start address, leading- and stride-dimension
+// byte offsets, swizzle mode (0: none, 2: 128-byte).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+    return uint64_t((saddr & 0x3FFFFu) >> 4) | (uint64_t((lbo >> 4) & 0x3FFFu) << 16) |
+           (uint64_t((sbo >> 4) & 0x3FFFu) << 32) | (uint64_t(1) << 46) | (uint64_t(swz & 7u) << 61);
 }
-__device__ __forceinline__ void lds128(uint32_t addr, uint32_t (&v)[4]) {
-    asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]) : "r"(addr));
+// Instruction descriptor, kind::f16: FP32 accumulators, BF16 A and B, B
+// K-major, A K-major (a_mn = 0) or MN-major (1), M = 128, N = n.
+__host__ __device__ constexpr uint32_t instr_desc(int n, uint32_t a_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (a_mn << 15) | (uint32_t(n >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 }
-// D += A B, m16n8k16, BF16 operands, FP32 accumulators.  Not volatile: the
-// compiler may interleave independent accumulations (a chain of MMAs on one
-// accumulator would otherwise wait out the pipe latency at every step).
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+// D (+)= A B^T on the tensor cores, issued by one thread
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate ? 1u : 0u)
+        : "memory");
+}
+// arrive on `bar` once every tensor-core operation this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 16 consecutive FP32 columns of this thread's tensor-memory lane (warp-wide)
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 // pull [src, src + bytes) into L2 ahead of its bulk copy into shared memory
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
@@ -235,7 +277,6 @@ struct Ring {
         atomicExch(abort_flag, 1);
         return false;
     }
-    __device__ bool aborted() const { return *reinterpret_cast<volatile int *>(abort_flag) != 0; }
 };
 
 // Cursor over the stages of the ring, kept identically by the producer and by
@@ -257,7 +298,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     constexpr int KP = 16 * MT;
     const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
     const int nwin = d.Cq / kWin;
-    const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = 8 * MT * kPlanesA * 256;
+    const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = kPlanesA * KP * 128;
     const uint32_t xbytes = uint32_t(KP) * (rows + kXPad) * 4;
     int pi = 0;  // next machine whose x_i tile is due
     // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory ring
@@ -270,8 +311,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
         mbar_arrive_expect_tx(&R.full[s], qbytes + zbytes);
         tma_load_1d(R.qslot(s), d.Q + q_block(d.Cq, d.npad, t, w), qbytes, &R.full[s], policy);
-        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Zfrag + size_t(8 * w) * MT * kPlanesA * 32, zbytes, &R.full[s],
-                    policy);
+        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Zop + size_t(w) * zbytes, zbytes, &R.full[s], policy);
         if (w + kPrefetch < nwin) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w + kPrefetch), qbytes);
         ++cur.q;
         // x_i tiles of the machines whose last chunk lies in this window
@@ -287,206 +327,183 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     }
 }
 
+// Tensor-core warp, sweep A: for every 16-column chunk of machine i,
+// D_b += Q[tile rows, chunk] Z[chunk, planes x rhs] into accumulator buffer
+// b = (machine count) mod 2, one M = 128 instruction per 128 rows of the tile
+// (A: the window block, 128-byte swizzled K-major; B: the z planes, core
+// matrices).  After the machine's last chunk the buffer is handed to the
+// consumers; a Q slot is released when the instructions reading it are done.
+// Heavy ball: one accumulation over every machine of the tile.
 template <int MT>
-__device__ void sweep_a_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool init, bool hb,
-                                 float gh, float gl) {
-    constexpr int KP = 16 * MT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tq = lane & 3;
+__device__ void sweep_a_mma(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
+                            const SysDesc &d, int row0, bool hb, uint32_t tmem) {
+    constexpr int NA = kPlanesA * 16 * MT;
+    constexpr uint32_t idesc = instr_desc(NA, 0);
     const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
-    const bool wact = 32 * warp < rows;
-    const int wrow = row0 + 32 * warp;  // first row of this warp
+    const int nmt = rows > 128 ? 2 : 1;
     const int nwin = d.Cq / kWin, nchunk = d.C / 16;
-    const int xstride = rows + kXPad;   // floats per right-hand side in an x_i tile
-    float xbh[MT][4][4], xbl[MT][4][4], S[MT][4][4], acc[MT][4][4];
-    // accumulator element e of (mt, nt): right-hand side 16 mt + g + 8 (e >> 1),
-    // row wrow + 8 nt + 2 tq + (e & 1)
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                S[mt][nt][e] = 0.0f;
-                acc[mt][nt][e] = 0.0f;
-                xbh[mt][nt][e] = 0.0f;
-                xbl[mt][nt][e] = 0.0f;
-            }
-    if (wact && !init && !hb) {
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int rhs = 16 * mt + g + 8 * h;
-                    const float4 v = __ldcg(reinterpret_cast<const float4 *>(
-                        d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq));  // {hi, lo} of two rows
-                    xbh[mt][nt][2 * h] = v.x;
-                    xbl[mt][nt][2 * h] = v.y;
-                    xbh[mt][nt][2 * h + 1] = v.z;
-                    xbl[mt][nt][2 * h + 1] = v.w;
-                }
-    }
-    int i = 0, iend = __ldg(d.coloff + 1) >> 4;  // machine of the current chunk, its end chunk
+    int i = 0, iend = __ldg(d.coloff + 1) >> 4;
+    bool first = true;
+    uint32_t b = 0;
     for (int w = 0; w < nwin; ++w) {
         const uint32_t s = cur.q % kQSlots;
         if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
+        tc_fence_after();
         const uint32_t sq = smem_u32(R.qslot(s)), sz = sq + kSlotQBytes;
-#pragma unroll 1
         for (int kc = 0; kc < 4; ++kc) {
             const int c16 = 4 * w + kc;
             if (c16 >= nchunk) break;
-            if (wact) {
-                uint32_t a[MT][kPlanesA][4];
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int p = 0; p < kPlanesA; ++p) {
-                        lds64(sz + (((2 * kc) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][0], a[mt][p][1]);
-                        lds64(sz + (((2 * kc + 1) * MT + mt) * kPlanesA + p) * 256 + lane * 8, a[mt][p][2],
-                              a[mt][p][3]);
-                    }
-                uint32_t b[4][2];
-#pragma unroll
-                for (int ntp = 0; ntp < 4; ntp += 2) {
-                    const int q = lane >> 3, r = lane & 7;
-                    const int row = 32 * warp + 8 * (ntp + (q >> 1)) + r;
-                    const int ch = 2 * kc + (q & 1);
-                    ldsm_x4(sq + row * 128 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
-                            b[ntp + 1][1]);
-                }
-#pragma unroll
-                for (int p = 0; p < kPlanesA; ++p)
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
+            if (first) {
+                b = mc & 1;
+                if (mc >= 2 && !R.wait(&dfree[b], ((mc >> 1) - 1) & 1)) return;
+                tc_fence_after();
             }
-            if (c16 + 1 == iend && hb) {
-                // heavy ball: the accumulator keeps summing over the machines
-                ++i;
-                if (i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
-            } else if (c16 + 1 == iend) {
-                // machine i is complete: x_i <- x_i + gamma (xbar - x_i - w_i), row sums
-                uint32_t xs = 0, sx = 0;
-                if (!init) {
-                    xs = cur.x % kXSlots;
-                    if (!R.wait(&R.xfull[xs], (cur.x / kXSlots) & 1)) return;
-                    sx = smem_u32(R.xslot(xs));
-                }
-                if (wact) {
-                    float *xg = d.X + x_block(d.m, KP, d.npad, t, i);
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const int rhs = 16 * mt + g + 8 * h;
-                                const int rr = 32 * warp + 8 * nt + 2 * tq;  // row within the tile
-                                uint32_t x0 = 0u, x1 = 0u;
-                                if (!init) lds64(sx + (rhs * xstride + rr) * 4, x0, x1);
-                                const float xo[2] = {__uint_as_float(x0), __uint_as_float(x1)};
-                                float xn[2];
-#pragma unroll
-                                for (int u = 0; u < 2; ++u) {
-                                    const int e = 2 * h + u;
-                                    const float v = ((xbh[mt][nt][e] - xo[u]) + xbl[mt][nt][e]) - acc[mt][nt][e];
-                                    xn[u] = upd_exact(xo[u], gh, gl, v);
-                                    S[mt][nt][e] += xn[u];
-                                    acc[mt][nt][e] = 0.0f;
-                                }
-                                __stcg(reinterpret_cast<float2 *>(xg + rhs * xstride + rr), make_float2(xn[0], xn[1]));
-                            }
-                }
-                if (!init) {
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&R.xempty[xs]);
-                    ++cur.x;
-                }
-                ++i;
-                if (i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
+            for (int h = 0; h < nmt; ++h)
+                tc_mma(tmem + uint32_t((2 * b + h) * NA), smem_desc(sq + h * 16384 + kc * 32, 16, 1024, 2),
+                       smem_desc(sz + kc * (NA * 32), 128, 256, 0), idesc, !first);
+            first = false;
+            if (hb ? c16 + 1 == nchunk : c16 + 1 == iend) {
+                tc_commit(&dfull[b]);
+                ++mc;
+                first = true;
+                if (!hb && ++i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
             }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&R.empty[s]);
+        tc_commit(&R.empty[s]);
         ++cur.q;
     }
+}
+
+// xbar' (FP32, the hi part) of row `row` split into three BF16 planes for
+// sweep B: element (plane p, right-hand side q) at op_offset(3 kp, p kp + q,
+// row); two adjacent rows (even lane, odd lane) go into one 32-bit store.
+template <int MT>
+__device__ void store_xop(const SysDesc &d, int64_t row, const float (&xo)[16 * MT]) {
+    constexpr int KP = 16 * MT, NB = kPlanesB * KP;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        const float x1 = __shfl_down_sync(0xffffffffu, xo[q], 1);
+        if ((lane & 1) == 0) {
+            uint32_t w[kPlanesB];
+            split2<kPlanesB>(xo[q], x1, w);
+#pragma unroll
+            for (int p = 0; p < kPlanesB; ++p)
+                __stcg(reinterpret_cast<uint32_t *>(d.Xop + op_offset(NB, p * KP + q, row)), w[p]);
+        }
+    }
+}
+
+// Consumers, sweep A: thread = one row of the tile (warp w: rows 128 (w/4) +
+// 32 (w%4) .. + 31, the tensor-memory lanes of its quarter).  Per machine:
+// w_i = the two planes' accumulators summed, then
+// x_i <- x_i + gamma (xbar - x_i - w_i) and the running row sum; at the end
+// the master's row update (double-float) and the xbar' planes of sweep B.
+template <int MT>
+__device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
+                                 const SysDesc &d, int row0, bool init, bool hb, float gh, float gl, uint32_t tmem) {
+    constexpr int KP = 16 * MT, NA = kPlanesA * KP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = warp >> 2, quad = warp & 3;
+    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    const int r = 128 * h + 32 * quad + lane;         // row within the tile
+    const bool wact = 128 * h + 32 * quad < rows;     // rows is a multiple of 32: warp-uniform
+    const int64_t grow = int64_t(row0) + r;           // row within the system
+    const uint32_t tl = tmem + (uint32_t(32 * quad) << 16);
+    float xbh[KP], xbl[KP], S[KP], W[KP];
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        xbh[q] = xbl[q] = S[q] = W[q] = 0.0f;
+    }
+    if (wact && !init && !hb) {
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            const float2 v = __ldcg(d.Xb + size_t(q) * d.npad + grow);
+            xbh[q] = v.x;
+            xbl[q] = v.y;
+        }
+    }
+    const int nm = hb ? 1 : d.m;
+    for (int i = 0; i < nm; ++i) {
+        const uint32_t b = mc & 1;
+        if (!R.wait(&dfull[b], (mc >> 1) & 1)) return;
+        tc_fence_after();
+        if (wact) {
+            const uint32_t col = uint32_t((2 * b + h) * NA);
+#pragma unroll
+            for (int c0 = 0; c0 < KP; c0 += 16) {
+                float p0[16], p1[16];
+                tc_ld16(tl + col + c0, p0);
+                tc_ld16(tl + col + KP + c0, p1);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) W[c0 + j] = p0[j] + p1[j];
+            }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&dfree[b]);
+        ++mc;
+        if (hb) break;
+        // machine i is complete: x_i <- x_i + gamma (xbar - x_i - w_i), row sums
+        uint32_t xs = 0, sx = 0;
+        if (!init) {
+            xs = cur.x % kXSlots;
+            if (!R.wait(&R.xfull[xs], (cur.x / kXSlots) & 1)) return;
+            sx = smem_u32(R.xslot(xs));
+        }
+        if (wact) {
+            float *xg = d.X + x_block(d.m, KP, d.npad, t, i);
+#pragma unroll
+            for (int q = 0; q < KP; ++q) {
+                const float xo = init ? 0.0f : lds_f32(sx + (q * rows + r) * 4);
+                const float v = ((xbh[q] - xo) + xbl[q]) - W[q];
+                const float xn = upd_exact(xo, gh, gl, v);
+                S[q] += xn;
+                __stcg(xg + size_t(q) * rows + r, xn);
+            }
+        }
+        if (!init) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&R.xempty[xs]);
+            ++cur.x;
+        }
+    }
     if (!wact) return;
-    float xo[MT][4][4];
+    float xo[KP];
     if (hb) {
         // heavy ball on the preconditioned system (Sec. 4.3 update, Sec. 6):
-        // the accumulator holds the gradient sum_i Q_i (Q_i^T x - c_i);
+        // W holds the gradient sum_i Q_i (Q_i^T x - c_i);
         // zeta <- beta zeta + gradient, x <- x - alpha zeta
         const float2 beta = make_float2(d.hb_hi, d.hb_lo), nalpha = make_float2(d.na_hi, d.na_lo);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int rhs = 16 * mt + g + 8 * h;
-                    const size_t off = size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq;
-                    const float4 xv = __ldcg(reinterpret_cast<const float4 *>(d.Xb + off));
-                    const float4 mv = __ldcg(reinterpret_cast<const float4 *>(d.Mb + off));
-                    const float2 x2[2] = {make_float2(xv.x, xv.y), make_float2(xv.z, xv.w)};
-                    const float2 m2[2] = {make_float2(mv.x, mv.y), make_float2(mv.z, mv.w)};
-                    float2 xn[2], zn[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        zn[u] = dfa(dfm(beta, m2[u]), make_float2(acc[mt][nt][2 * h + u], 0.0f));
-                        xn[u] = dfa(x2[u], dfm(nalpha, zn[u]));
-                        xo[mt][nt][2 * h + u] = xn[u].x;
-                    }
-                    __stcg(reinterpret_cast<float4 *>(d.Mb + off), make_float4(zn[0].x, zn[0].y, zn[1].x, zn[1].y));
-                    __stcg(reinterpret_cast<float4 *>(d.Xb + off), make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
-                }
+        for (int q = 0; q < KP; ++q) {
+            const size_t off = size_t(q) * d.npad + grow;
+            const float2 zn = dfa(dfm(beta, __ldcg(d.Mb + off)), make_float2(W[q], 0.0f));
+            const float2 xn = dfa(__ldcg(d.Xb + off), dfm(nalpha, zn));
+            __stcg(d.Mb + off, zn);
+            __stcg(d.Xb + off, xn);
+            xo[q] = xn.x;
+        }
     } else {
         // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
         const float2 em = make_float2(init ? d.im_hi : d.em_hi, init ? d.im_lo : d.em_lo);
         const float2 e1 = make_float2(d.e1_hi, d.e1_lo);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    float2 xn[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int e = 2 * h + u;
-                        xn[u] = dfm(em, make_float2(S[mt][nt][e], 0.0f));
-                        if (!init) xn[u] = dfa(xn[u], dfm(e1, make_float2(xbh[mt][nt][e], xbl[mt][nt][e])));
-                        xo[mt][nt][e] = xn[u].x;
-                    }
-                    const int rhs = 16 * mt + g + 8 * h;
-                    __stcg(reinterpret_cast<float4 *>(d.Xb + size_t(rhs) * d.npad + wrow + 8 * nt + 2 * tq),
-                           make_float4(xn[0].x, xn[0].y, xn[1].x, xn[1].y));
-                }
-    }
-    // xbar' operand planes of sweep B: in the 16-row chunk kc of this warp,
-    // a0/a1 are n-tile 2kc (rhs g / g+8) and a2/a3 n-tile 2kc+1
-#pragma unroll
-    for (int kc = 0; kc < 2; ++kc)
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-            uint32_t w0[kPlanesB], w1[kPlanesB], w2[kPlanesB], w3[kPlanesB];
-            split2<kPlanesB>(xo[mt][2 * kc][0], xo[mt][2 * kc][1], w0);
-            split2<kPlanesB>(xo[mt][2 * kc][2], xo[mt][2 * kc][3], w1);
-            split2<kPlanesB>(xo[mt][2 * kc + 1][0], xo[mt][2 * kc + 1][1], w2);
-            split2<kPlanesB>(xo[mt][2 * kc + 1][2], xo[mt][2 * kc + 1][3], w3);
-            const size_t kcg = size_t(wrow >> 4) + kc;
-#pragma unroll
-            for (int p = 0; p < kPlanesB; ++p)
-                __stcg(d.Xfrag + ((kcg * MT + mt) * kPlanesB + p) * 32 + lane, make_uint4(w0[p], w1[p], w2[p], w3[p]));
+        for (int q = 0; q < KP; ++q) {
+            float2 xn = dfm(em, make_float2(S[q], 0.0f));
+            if (!init) xn = dfa(xn, dfm(e1, make_float2(xbh[q], xbl[q])));
+            __stcg(d.Xb + size_t(q) * d.npad + grow, xn);
+            xo[q] = xn.x;
         }
+    }
+    store_xop<MT>(d, grow, xo);
 }
 
 // ---- sweep B -----------------------------------------------------------------------
 template <int MT>
 __device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, uint64_t policy) {
     const int nwin = min(kColsB, d.Cq - col0) / kWin;
-    const uint32_t xbytes = 2 * MT * kPlanesB * 512;
+    const uint32_t xbytes = kPlanesB * 16 * MT * 64;  // 32 rows
     for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
@@ -496,80 +513,99 @@ __device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
             tma_load_1d(R.qslot(s) + j * (kRowsStageB * kWin * 2),
                         d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin,
                         kRowsStageB * kWin * 2, &R.full[s], policy);
-        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xfrag + size_t(r0 >> 4) * MT * kPlanesB * 32, xbytes, &R.full[s],
+        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xop + size_t(r0) * (xbytes / kRowsStageB), xbytes, &R.full[s],
                     policy);
         ++cur.q;
     }
 }
 
+// z = Y - c of column `col` split into two BF16 planes for sweep A: element
+// (plane p, right-hand side q) at op_offset(2 kp, p kp + q, col); two adjacent
+// columns (even lane, odd lane) go into one 32-bit store.  zero_y: z = -c.
 template <int MT>
-__device__ void store_z(const SysDesc &d, int col0, float (&acc)[MT][8][4], bool zero_y) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ void store_z(const SysDesc &d, int col, const float (&Y)[16 * MT], bool zero_y) {
+    constexpr int KP = 16 * MT, NA = kPlanesA * KP;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-            const size_t G = size_t(col0 >> 3) + 8 * warp + nt;
-            const float4 c = __ldg(d.Cfrag + (G * MT + mt) * 32 + lane);
-            const float y0 = zero_y ? 0.0f : acc[mt][nt][0], y1 = zero_y ? 0.0f : acc[mt][nt][1];
-            const float y2 = zero_y ? 0.0f : acc[mt][nt][2], y3 = zero_y ? 0.0f : acc[mt][nt][3];
-            uint32_t w01[kPlanesA], w23[kPlanesA];
-            split2<kPlanesA>(y0 - c.x, y1 - c.y, w01);
-            split2<kPlanesA>(y2 - c.z, y3 - c.w, w23);
+    for (int q = 0; q < KP; ++q) {
+        const float z = (zero_y ? 0.0f : Y[q]) - __ldg(d.Ct + size_t(q) * d.Cq + col);
+        const float z1 = __shfl_down_sync(0xffffffffu, z, 1);
+        if ((lane & 1) == 0) {
+            uint32_t w[kPlanesA];
+            split2<kPlanesA>(z, z1, w);
 #pragma unroll
             for (int p = 0; p < kPlanesA; ++p)
-                __stcg(d.Zfrag + ((G * MT + mt) * kPlanesA + p) * 32 + lane, make_uint2(w01[p], w23[p]));
+                __stcg(reinterpret_cast<uint32_t *>(d.Zop + op_offset(NA, p * KP + q, col)), w[p]);
         }
+    }
 }
 
+// Tensor-core warp, sweep B: D_h += Q[rows, 128 columns]^T Xop[rows, planes x
+// rhs] for the unit's M-tiles h (A: the stage's 64-column blocks read
+// MN-major, 128-byte swizzle, 4 KB between blocks; B: the xbar' planes, core
+// matrices), over all row stages; the accumulators go to the consumers once
+// per unit and are reused after they release them.
 template <int MT>
-__device__ void sweep_b_consumer(const Ring &R, Cursor &cur, const SysDesc &d, int col0) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool wact = 64 * warp < min(kColsB, d.Cq - col0);
-    float acc[MT][8][4];
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+__device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree,
+                            const SysDesc &d, int col0, uint32_t tmem) {
+    constexpr int NB = kPlanesB * 16 * MT;
+    constexpr uint32_t idesc = instr_desc(NB, 1);
+    const int nmt = (min(kColsB, d.Cq - col0) + 127) / 128;
+    if (ubc > 0 && !R.wait(bfree, (ubc - 1) & 1)) return;
+    tc_fence_after();
+    bool first = true;
     for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
         const uint32_t s = cur.q % kQSlots;
         if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
-        if (wact) {
-            // this warp's 64 columns: a [32][64] block, chunks XOR-permuted by (row & 7)
-            const uint32_t sq = smem_u32(R.qslot(s)) + warp * (kRowsStageB * kWin * 2);
-            const uint32_t sx = smem_u32(R.qslot(s)) + kSlotQBytes;
+        tc_fence_after();
+        const uint32_t sq = smem_u32(R.qslot(s)), sx = sq + kSlotQBytes;
 #pragma unroll
-            for (int kc = 0; kc < 2; ++kc) {
-                uint32_t a[MT][kPlanesB][4];
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int p = 0; p < kPlanesB; ++p)
-                        lds128(sx + ((kc * MT + mt) * kPlanesB + p) * 512 + lane * 16, a[mt][p]);
-                uint32_t b[8][2];
-#pragma unroll
-                for (int ntp = 0; ntp < 8; ntp += 2) {
-                    const int q = lane >> 3, r = lane & 7;
-                    const int row = 16 * kc + 8 * (q & 1) + r;
-                    const int ch = ntp + (q >> 1);
-                    ldsm_x4_t(sq + row * 128 + ((ch ^ (row & 7)) << 4), b[ntp][0], b[ntp][1], b[ntp + 1][0],
-                              b[ntp + 1][1]);
-                }
-#pragma unroll
-                for (int p = 0; p < kPlanesB; ++p)
-#pragma unroll
-                    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                        for (int nt = 0; nt < 8; ++nt) mma_bf16(acc[mt][nt], a[mt][p], b[nt][0], b[nt][1]);
-            }
+        for (int ks = 0; ks < kRowsStageB / 16; ++ks) {
+            for (int h = 0; h < nmt; ++h)
+                tc_mma(tmem + uint32_t(h * NB), smem_desc(sq + 2 * h * 4096 + ks * 2048, 4096, 1024, 2),
+                       smem_desc(sx + ks * (NB * 32), 128, 256, 0), idesc, !first);
+            first = false;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&R.empty[s]);
+        tc_commit(&R.empty[s]);
         ++cur.q;
     }
-    if (wact) store_z<MT>(d, col0, acc, false);
+    tc_commit(bfull);
+    ++ubc;
+}
+
+// Consumers, sweep B: thread = one column (warp w: M-tiles w/4 and w/4 + 2,
+// columns 32 (w%4) .. + 31 of each, the tensor-memory lanes of its quarter):
+// Y = the three planes' accumulators summed, then z = Y - c to sweep A.
+template <int MT>
+__device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree, const SysDesc &d,
+                                 int col0, uint32_t tmem) {
+    constexpr int KP = 16 * MT, NB = kPlanesB * KP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3;
+    const int ncols = min(kColsB, d.Cq - col0);
+    if (!R.wait(bfull, ubc & 1)) return;
+    tc_fence_after();
+    const uint32_t tl = tmem + (uint32_t(32 * quad) << 16);
+#pragma unroll 1
+    for (int hh = 0; hh < 2; ++hh) {
+        const int h = (warp >> 2) + 2 * hh;
+        const int cl = 128 * h + 32 * quad;  // ncols is a multiple of 64: warp-uniform
+        if (cl >= ncols) continue;
+        float Y[KP];
+#pragma unroll
+        for (int c0 = 0; c0 < KP; c0 += 16) {
+            float p0[16], p1[16], p2[16];
+            tc_ld16(tl + uint32_t(h * NB + c0), p0);
+            tc_ld16(tl + uint32_t(h * NB + KP + c0), p1);
+            tc_ld16(tl + uint32_t(h * NB + 2 * KP + c0), p2);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) Y[c0 + j] = (p0[j] + p1[j]) + p2[j];
+        }
+        store_z<MT>(d, col0 + cl + lane, Y, false);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bfree);
+    ++ubc;
 }
 
 // Bounded grid barrier over all CTAs: false when the wait ran out of time.
@@ -595,21 +631,29 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t target, uint64_t timeout_ns
 
 template <int MT>
 __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs a) {
-    extern __shared__ __align__(128) uint8_t smem[];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ int abort_flag;
+    // the 128-byte swizzle is applied to absolute shared addresses: slots start on 1024 bytes
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kBarOffset);
     Ring R{smem, bars, bars + kQSlots, bars + 2 * kQSlots, bars + 2 * kQSlots + kXSlots, &abort_flag,
            a.timeout_ns};
     uint64_t *uqfull = bars + 2 * kQSlots + 2 * kXSlots;  // [kUQ] a claimed unit is in the queue
-    uint64_t *uqempty = uqfull + kUQ;                     // [kUQ] every consumer warp has read it
-    volatile int *uq = reinterpret_cast<volatile int *>(uqempty + kUQ);
+    uint64_t *uqempty = uqfull + kUQ;                     // [kUQ] consumers and tensor-core warp have read it
+    uint64_t *dfull = uqempty + kUQ;                      // [2] sweep-A accumulator buffer ready
+    uint64_t *dfree = dfull + 2;                          // [2] sweep-A accumulator buffer read
+    uint64_t *bfull = dfree + 2, *bfree = bfull + 1;      // sweep-B accumulators ready / read
+    uint64_t *drain = bfree + 1;                          // every tensor-core operation done (exit)
+    volatile int *uq = reinterpret_cast<volatile int *>(drain + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1) + kUQ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool producer = warp == kConsumerWarps;
+    const bool producer = warp == kProducerWarp, mma_warp = warp == kMmaWarp;
+    const bool consumer = warp < kConsumerWarps;
     if (threadIdx.x == 0) {
         abort_flag = 0;
         for (int s = 0; s < kQSlots; ++s) {
             mbar_init(&R.full[s], 1);
-            mbar_init(&R.empty[s], kConsumerWarps);
+            mbar_init(&R.empty[s], 1);  // tcgen05.commit of the instructions that read the slot
         }
         for (int s = 0; s < kXSlots; ++s) {
             mbar_init(&R.xfull[s], 1);
@@ -617,21 +661,39 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
         }
         for (int s = 0; s < kUQ; ++s) {
             mbar_init(&uqfull[s], 1);
-            mbar_init(&uqempty[s], kConsumerWarps);
+            mbar_init(&uqempty[s], kConsumerWarps + 1);
         }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&dfull[s], 1);
+            mbar_init(&dfree[s], kConsumerWarps);
+        }
+        mbar_init(bfull, 1);
+        mbar_init(bfree, kConsumerWarps);
+        mbar_init(drain, 1);
         fence_mbar_init_cluster();
     }
+    if (mma_warp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "n"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tmem_slot);
     const uint64_t policy = policy_evict_first();
     Cursor cur;
-    uint32_t uk = 0;  // units handed over so far (same count in the producer and every consumer warp)
+    uint32_t uk = 0;   // units handed over so far (same count in every role)
+    uint32_t mc = 0;   // sweep-A accumulations (machines) so far (tensor-core warp and consumers)
+    uint32_t ubc = 0;  // sweep-B units so far (tensor-core warp and consumers)
     uint32_t episode = 0;
     bool ok = true;
 
     // One sweep.  The CTAs claim units from a global counter (the lists are
     // sorted longest first, so this is list scheduling with the longest units
     // first and the imbalance at the grid barrier is at most the shortest
-    // units).  The producer claims ahead of the consumers and hands each unit
+    // units).  The producer claims ahead of the other roles and hands each unit
     // over through a small queue, so the ring keeps streaming across unit
     // boundaries; a claim past the end hands over -1 and ends the sweep.
     auto sweep = [&](bool is_a, uint32_t e, bool init, bool hb) {
@@ -656,6 +718,19 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 if (is_a) sweep_a_producer<MT>(R, cur, a.sys[U.x], U.y, init || hb, policy);
                 else sweep_b_producer<MT>(R, cur, a.sys[U.x], U.y, policy);
             }
+        } else if (mma_warp) {
+            if (lane != 0) return;
+            for (;;) {
+                const int s = int(uk % kUQ);
+                if (!R.wait(&uqfull[s], (uk / kUQ) & 1)) return;
+                const int u = uq[s];
+                mbar_arrive(&uqempty[s]);
+                ++uk;
+                if (u < 0) return;
+                const int2 U = units[u];
+                if (is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, a.sys[U.x], U.y, hb, tmem);
+                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, a.sys[U.x], U.y, tmem);
+            }
         } else {
             for (;;) {
                 const int s = int(uk % kUQ);
@@ -667,8 +742,11 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 if (u < 0) return;
                 const int2 U = units[u];
                 const SysDesc &d = a.sys[U.x];
-                if (is_a) sweep_a_consumer<MT>(R, cur, d, U.y, init, hb, init ? 1.0f : d.g_hi, init ? 0.0f : d.g_lo);
-                else sweep_b_consumer<MT>(R, cur, d, U.y);
+                if (is_a)
+                    sweep_a_consumer<MT>(R, cur, mc, dfull, dfree, d, U.y, init, hb, init ? 1.0f : d.g_hi,
+                                         init ? 0.0f : d.g_lo, tmem);
+                else
+                    sweep_b_consumer<MT>(R, ubc, bfull, bfree, d, U.y, tmem);
             }
         }
     };
@@ -676,13 +754,17 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     if (a.init) {
         // z_i(0) = -c_i, so that sweep A with gamma = 1 and x = xbar = 0 forms
         // the least-norm x_i(0) = Q_i c_i (Algorithm 1) and xbar(0) their mean
-        if (!producer)
+        if (consumer)
             for (int u = blockIdx.x; u < a.nB; u += gridDim.x) {
                 const int2 U = a.unitsB[u];
                 const SysDesc &d = a.sys[U.x];
-                if (64 * warp < min(kColsB, d.Cq - U.y)) {
-                    float acc[MT][8][4] = {};
-                    store_z<MT>(d, U.y, acc, true);
+                const int ncols = min(kColsB, d.Cq - U.y);
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int cl = 128 * ((warp >> 2) + 2 * hh) + 32 * (warp & 3);
+                    if (cl < ncols) {
+                        float Y[16 * MT] = {};
+                        store_z<MT>(d, U.y + cl + lane, Y, true);
+                    }
                 }
             }
         ++episode;
@@ -699,8 +781,10 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
             ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
         }
     }
-    // no bulk copy may still be writing this CTA's shared memory at exit: the
-    // producer waits (bounded) for the last phase of every slot it filled
+    // no bulk copy may still be writing this CTA's shared memory and no
+    // tensor-core operation may still be using tensor memory at exit: the
+    // producer waits (bounded) for the last phase of every slot it filled, the
+    // tensor-core warp for a final commit
     __syncthreads();
     if (producer && lane == 0) {
         for (uint32_t q = cur.q > uint32_t(kQSlots) ? cur.q - kQSlots : 0; q < cur.q; ++q)
@@ -708,7 +792,15 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
         for (uint32_t x = cur.x > uint32_t(kXSlots) ? cur.x - kXSlots : 0; x < cur.x; ++x)
             (void)mbar_wait(&R.xfull[x % kXSlots], (x / kXSlots) & 1, a.timeout_ns);
     }
+    if (mma_warp && lane == 0) {
+        tc_commit(drain);
+        (void)mbar_wait(drain, 0, a.timeout_ns);
+    }
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    if (mma_warp)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
     if (threadIdx.x == 0 && abort_flag) atomicCAS(a.err, 0, DEV_TIMEOUT_GRID);
 }
 
@@ -734,12 +826,10 @@ __global__ void repack_kernel(const __nv_bfloat16 *Qs, int64_t n, int m, int P, 
 }
 
 // c_b = R2^T R1^T (d .* B_b) for one right-hand side (grid m x k), written as
-// FP32 into the accumulator-fragment order of sweep B: column col and
-// right-hand side rhs go to group col/8, m-tile rhs/16, lane 4 (rhs%8) +
-// (col%8)/2, element 2 ((rhs%16)/8) + col%2.
+// FP32 into Ct[rhs][column] (Cq columns per right-hand side).
 __global__ void batch_coef_kernel(const double *B, int k, const int64_t *row_start, const int32_t *pcount,
                                   const double *dinv, const double *Rinv1, const double *Rinv2, int P,
-                                  const int *coloff, int MT, float *Cfrag) {
+                                  const int *coloff, int Cq, float *Ct) {
     extern __shared__ double sh[];  // y[P], u[P]
     const int b = blockIdx.x, rhs = blockIdx.y;
     const int p = pcount[b];
@@ -757,10 +847,7 @@ __global__ void batch_coef_kernel(const double *B, int k, const int64_t *row_sta
     for (int c = threadIdx.x; c < p; c += blockDim.x) {
         double s = 0.0;
         for (int r = 0; r <= c; ++r) s = fma(R2[size_t(r) * P + c], u[r], s);
-        const int col = coloff[b] + c;
-        const int G = col >> 3, w = col & 7;
-        const int mt = rhs >> 4, rr = rhs & 15;
-        Cfrag[((size_t(G) * MT + mt) * 32 + (rr & 7) * 4 + (w >> 1)) * 4 + (rr >> 3) * 2 + (w & 1)] = float(s);
+        Ct[size_t(rhs) * Cq + coloff[b] + c] = float(s);
     }
 }
 
@@ -902,12 +989,11 @@ int check_err(apc_batch *b, cudaStream_t s) {
 int compute_coefficients(apc_batch *b, int sys, cudaStream_t s) {
     apc_ctx *c = b->ctx[sys];
     const SysDesc &d = b->desc[sys];
-    float4 *Cf = const_cast<float4 *>(d.Cfrag);
-    BCK(b, cudaMemsetAsync(Cf, 0, sizeof(float4) * size_t(d.Cq / 8) * b->MT * 32, s));
+    float *Ct = const_cast<float *>(d.Ct);
+    BCK(b, cudaMemsetAsync(Ct, 0, sizeof(float) * size_t(b->kp) * d.Cq, s));
     const size_t sh = sizeof(double) * 2 * c->P;
     batch_coef_kernel<<<dim3(unsigned(c->m), unsigned(b->k)), 128, sh, s>>>(
-        b->B[sys], b->k, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->P, d.coloff, b->MT,
-        reinterpret_cast<float *>(Cf));
+        b->B[sys], b->k, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->P, d.coloff, d.Cq, Ct);
     BCK(b, cudaGetLastError());
     return APC_OK;
 }
@@ -997,20 +1083,20 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         const size_t x_elems = x_block(m, kp, int(npad), ntiles, 0);
         int *d_co = nullptr, *d_cb = nullptr;
         __nv_bfloat16 *Q = nullptr;
-        float4 *Cf = nullptr;
+        float *Cf = nullptr;
         double *Bc = nullptr;
         if ((rc = balloc(b, &d_co, sizeof(int) * (m + 1))) || (rc = balloc(b, &d_cb, sizeof(int) * (Cq / 16))) ||
             (rc = balloc(b, &Q, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
             (rc = balloc(b, &d.X, sizeof(float) * x_elems)) ||
             (rc = balloc(b, &d.Xb, sizeof(float2) * size_t(kp) * npad)) ||
-            (rc = balloc(b, &d.Xfrag, sizeof(uint4) * size_t(npad / 16) * MT * kPlanesB * 32)) ||
-            (rc = balloc(b, &d.Zfrag, sizeof(uint2) * size_t(Cq / 8) * MT * kPlanesA * 32)) ||
-            (rc = balloc(b, &Cf, sizeof(float4) * size_t(Cq / 8) * MT * 32)) ||
+            (rc = balloc(b, &d.Xop, size_t(npad) * kPlanesB * kp * 2)) ||
+            (rc = balloc(b, &d.Zop, size_t(Cq) * kPlanesA * kp * 2)) ||
+            (rc = balloc(b, &Cf, sizeof(float) * size_t(kp) * Cq)) ||
             (rc = balloc(b, &d.Mb, sizeof(float2) * size_t(kp) * npad)) ||
             (rc = balloc(b, &Bc, sizeof(double) * size_t(n) * k)))
             return bail(rc);
         d.Q = Q;
-        d.Cfrag = Cf;
+        d.Ct = Cf;
         d.coloff = d_co;
         b->B.push_back(Bc);
         b->q_bytes += int64_t(sizeof(__nv_bfloat16)) * npad * Cq;
@@ -1021,6 +1107,8 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         cudaMemsetAsync(d.X, 0, sizeof(float) * x_elems, s);
         cudaMemsetAsync(d.Xb, 0, sizeof(float2) * size_t(kp) * npad, s);
         cudaMemsetAsync(d.Mb, 0, sizeof(float2) * size_t(kp) * npad, s);
+        cudaMemsetAsync(d.Xop, 0, size_t(npad) * kPlanesB * kp * 2, s);
+        cudaMemsetAsync(d.Zop, 0, size_t(Cq) * kPlanesA * kp * 2, s);
         const unsigned grid = unsigned(std::min<int64_t>((npad * Cq + 255) / 256, 152 * 32));
         repack_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->Q), n, m, c->P, d_cb, d_co, c->d_p,
                                            int(npad), Cq, Q);
