@@ -219,6 +219,27 @@ int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_it
 int apc_backward(apc_ctx *ctx, const double *g_dev, int64_t T, double gamma, double eta, double *db_dev,
                  void *stream);
 
+/* apc_backward_params -- apc_backward plus the derivatives of L with respect
+ * to gamma and eta.  The paper prints no formula for these; they are the
+ * reverse-mode derivative of Eq. (cons): with mu_i = lambda_i + (eta/m) lbar at
+ * step t+1 and the forward states x_i(t), xbar(t),
+ *   dL/dgamma = sum_t sum_i <mu_i(t+1), P_i (xbar(t) - x_i(t))>
+ *             = (1/gamma) sum_t sum_i <mu_i(t+1), x_i(t+1) - x_i(t)>,
+ *   dL/deta   = sum_t <lbar(t+1), (1/m) sum_i x_i(t+1) - xbar(t)>.
+ * These need the forward trajectory, which (unlike dL/db) depends on b:
+ *   b_dev      : N, FP64, device, caller's row order; NULL = the b of apc_setup.
+ *   ckpt_every : the forward states are kept every ckpt_every iterations
+ *                (0 = 20) and recomputed from there, one segment at a time,
+ *                during the reverse sweep: device memory for ceil(T/ckpt_every)
+ *                checkpoints and ckpt_every + 1 states (each m n + n values),
+ *                allocated and freed by the call, and ~T more forward steps.
+ *   db_dev     : as apc_backward.  dgamma_host, deta_host: host doubles.
+ * Uses the context's iteration state (a later apc_iterate needs apc_reset).
+ * Errors: PARAMS, INVALID_ARG, NOMEM, TIMEOUT, CUDA. */
+int apc_backward_params(apc_ctx *ctx, const double *g_dev, const double *b_dev, int64_t T, double gamma,
+                        double eta, int32_t ckpt_every, double *db_dev, double *dgamma_host, double *deta_host,
+                        void *stream);
+
 /* apc_set_test_hooks -- failure injection for tests, on the host side of a
  * device wait: every grid barrier of later launches waits for
  * grid_barrier_skew arrivals more than the grid has (0 = normal), and every

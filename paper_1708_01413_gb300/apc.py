@@ -25,7 +25,7 @@ ERRORS = {
 # Every function the header declares; tests check the library exports them.
 EXPORTED = (
     "apc_setup", "apc_optimal_params", "apc_reset", "apc_iterate", "apc_get_xbar", "apc_get_x",
-    "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
+    "apc_get_basis", "apc_residual", "apc_solve", "apc_backward", "apc_backward_params", "apc_set_test_hooks", "apc_context_info", "apc_last_error", "apc_destroy",
     "apc_spectral_bounds", "apc_setup_rows", "apc_hb_optimal_params", "apc_batch_set_hb_params",
     "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
@@ -76,6 +76,7 @@ def lib() -> C.CDLL:
     L.apc_context_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i32),
                                    C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]
     L.apc_backward.argtypes = [vp, vp, i64, dbl, dbl, vp, vp]
+    L.apc_backward_params.argtypes = [vp, vp, vp, i64, dbl, dbl, i32, vp, C.POINTER(dbl), C.POINTER(dbl), vp]
     L.apc_set_test_hooks.argtypes = [vp, i32, dbl]
     L.apc_spectral_bounds.argtypes = [vp, i32, C.c_uint64, C.POINTER(dbl), C.POINTER(dbl), vp]
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
@@ -220,6 +221,20 @@ class Context:
         _check(lib().apc_backward(self.handle, _ptr(g.contiguous()), int(T), gamma, eta, _ptr(out),
                                   _stream(stream)), self.handle)
         return out
+
+    def backward_params(self, g, T: int, gamma: float, eta: float, b=None, ckpt_every: int = 20, out=None,
+                        stream=None):
+        """(dL/db, dL/dgamma, dL/deta) through T iterations from the least-norm
+        start for right-hand side b (None: the b of set-up); the forward states
+        are recomputed from checkpoints every ``ckpt_every`` iterations."""
+        import torch
+        N = self.info()["N"]
+        out = torch.empty(N, dtype=torch.float64, device=self.device) if out is None else out
+        dg, de = C.c_double(), C.c_double()
+        _check(lib().apc_backward_params(self.handle, _ptr(g.contiguous()), _ptr(b.contiguous() if b is not None else None),
+                                         int(T), gamma, eta, int(ckpt_every), _ptr(out), C.byref(dg), C.byref(de),
+                                         _stream(stream)), self.handle)
+        return out, dg.value, de.value
 
     def solve(self, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False,
               out=None, stream=None, raise_on_error=True):

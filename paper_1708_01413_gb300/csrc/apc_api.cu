@@ -620,6 +620,117 @@ int apc_backward(apc_ctx *c, const double *g_dev, int64_t T, double gamma, doubl
     return APC_OK;
 }
 
+int apc_backward_params(apc_ctx *c, const double *g_dev, const double *b_dev, int64_t T, double gamma, double eta,
+                        int32_t ckpt_every, double *db_dev, double *dgamma_host, double *deta_host, void *stream) {
+    if (!c || !g_dev || !db_dev || !dgamma_host || !deta_host || T < 0 || ckpt_every < 0)
+        return fail(c, APC_ERR_INVALID_ARG, "bad argument");
+    if (!(gamma > 0.0 && gamma < 2.0) || !std::isfinite(eta))
+        return fail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2) and eta must be finite", gamma);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t C = std::max<int64_t>(1, std::min<int64_t>(ckpt_every > 0 ? ckpt_every : 20, std::max<int64_t>(T, 1)));
+    const int64_t nseg = (T + C - 1) / C;
+    const size_t ssz = s_elem_size(c->precision);
+    const size_t xs = ssz * size_t(c->n) * c->m, xbs = sizeof(double) * size_t(c->n);
+    const size_t zs = ssz * 3 * size_t(c->m) * c->P, st = xs + xbs + zs;
+    char *ck = nullptr, *seg = nullptr, *save = nullptr;
+    double *acc = nullptr;
+    std::vector<int64_t> ck_t(size_t(std::max<int64_t>(nseg, 1)), 0);
+    auto release = [&]() {
+        cudaFree(ck);
+        cudaFree(seg);
+        cudaFree(save);
+        cudaFree(acc);
+    };
+    if (cudaMalloc(&ck, st * size_t(std::max<int64_t>(nseg, 1))) != cudaSuccess ||
+        cudaMalloc(&seg, (xs + xbs) * size_t(C + 1)) != cudaSuccess || cudaMalloc(&save, st) != cudaSuccess ||
+        cudaMalloc(&acc, 2 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return fail(c, APC_ERR_NOMEM, "apc_backward_params: cannot allocate %lld checkpoints",
+                    (long long)nseg);
+    }
+    // copies of the iteration state (machines' iterates, master, z buffers, pass counter)
+    auto put = [&](char *dst) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, c->xw, xs, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + xs, c->xbar, xbs, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst + xs + xbs, c->zbuf, zs, cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    auto get = [&](const char *src) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(c->xw, src, xs, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->xbar, src + xs, xbs, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->zbuf, src + xs + xbs, zs, cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    auto seg_state = [&](int64_t j) { return seg + size_t(j) * (xs + xbs); };
+    auto keep = [&](int64_t j) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(seg_state(j), c->xw, xs, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(seg_state(j) + xs, c->xbar, xbs, cudaMemcpyDeviceToDevice, s);
+        return e;
+    };
+    int rc = APC_OK;
+    auto body = [&]() -> int {
+        int r;
+        // forward from the least-norm start, a checkpoint every C iterations
+        const double *rhs = b_dev;
+        if (b_dev && c->d_perm) {
+            CK(c, launch_permute_vec(b_dev, c->d_perm, c->N, 0, c->rtmp, s));
+            rhs = c->rtmp;
+        }
+        if ((r = reset_blocked(c, rhs, s)) != APC_OK) return r;
+        for (int64_t k = 0; k < nseg; ++k) {
+            CK(c, put(ck + size_t(k) * st));
+            ck_t[size_t(k)] = c->t;
+            if (k + 1 < nseg && (r = run_pass(c, MODE_APC, gamma, eta, C, s)) != APC_OK) return r;
+        }
+        // reverse sweep (apc_backward), one transposed step at a time
+        CK(c, cudaMemsetAsync(c->xw, 0, xs, s));
+        CK(c, cudaMemsetAsync(c->zbuf, 0, zs, s));
+        CK(c, cudaMemcpyAsync(c->xbar, g_dev, xbs, cudaMemcpyDeviceToDevice, s));
+        CK(c, cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
+        c->t = 0;
+        if ((r = run_pass(c, MODE_ADJ_SEED, gamma, eta, 1, s)) != APC_OK) return r;
+        for (int64_t k = nseg - 1; k >= 0; --k) {
+            const int64_t t0 = k * C, len = std::min(T, t0 + C) - t0;
+            // forward states t0 .. t0 + len from the checkpoint, the reverse state set aside
+            CK(c, put(save));
+            const int64_t t_adj = c->t;
+            CK(c, get(ck + size_t(k) * st));
+            c->t = ck_t[size_t(k)];
+            CK(c, keep(0));
+            for (int64_t j = 1; j <= len; ++j) {
+                if ((r = run_pass(c, MODE_APC, gamma, eta, 1, s)) != APC_OK) return r;
+                CK(c, keep(j));
+            }
+            CK(c, get(save));
+            c->t = t_adj;
+            for (int64_t j = len - 1; j >= 0; --j) {
+                // lambda_i(t+1), lbar(t+1) are the state before the transposed step for t = t0 + j
+                CK(c, launch_adj_dots(c->xw, c->xbar, seg_state(j + 1), seg_state(j), reinterpret_cast<const double *>(
+                                          seg_state(j) + xs), c->n, c->m, eta / c->m, state_prec(c->precision), acc, s));
+                if ((r = run_pass(c, MODE_ADJ, gamma, eta, 1, s)) != APC_OK) return r;
+            }
+        }
+        // v_i = Q_i^T (lambda_i(0) + lbar(0)/m), db_i = (A_i^+)^T-part as in apc_backward
+        if ((r = run_pass(c, MODE_ADJ_FINAL, gamma, eta, 1, s)) != APC_OK) return r;
+        const void *v = static_cast<const char *>(c->zbuf) + ssz * size_t(c->t % 3) * c->m * c->P;
+        CK(c, launch_bsolve(v, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P,
+                            state_prec(c->precision), c->d_perm ? c->rtmp : db_dev, s));
+        if (c->d_perm) CK(c, launch_permute_vec(c->rtmp, c->d_perm, c->N, 1, db_dev, s));
+        double h[2];
+        CK(c, cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+        CK(c, cudaStreamSynchronize(s));
+        *dgamma_host = h[0] / gamma;
+        *deta_host = h[1];
+        return APC_OK;
+    };
+    rc = body();
+    cudaStreamSynchronize(s);
+    release();
+    c->t = 0;  // the iteration state now holds the reverse sweep: apc_iterate needs apc_reset
+    return rc;
+}
+
 int apc_set_test_hooks(apc_ctx *c, int32_t grid_barrier_skew, double timeout_s) {
     if (!c || grid_barrier_skew < 0 || !(timeout_s > 0.0)) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
     c->test_barrier_skew = uint32_t(grid_barrier_skew);

@@ -104,6 +104,10 @@ cudaError_t launch_unpack_x(const void *xw, int precision, int64_t n, int m, dou
 cudaError_t launch_get_basis(const void *Q, int precision, int64_t n, int m, int P, int b, int p, double *out,
                              int64_t ldq, cudaStream_t s);
 cudaError_t launch_axpy_f64(double *y, const double *x, double a, int64_t count, cudaStream_t s);
+// acc[0] += sum (lam + em lbar) . (x1 - x0) over the [n][m] states,
+// acc[1] += lbar . (mean_i x1 - xb0)   (precision: 0 = FP64 states, 1 = FP32)
+cudaError_t launch_adj_dots(const void *lam, const double *lbar, const void *x1, const void *x0, const double *xb0,
+                            int64_t n, int m, double em, int precision, double *acc, cudaStream_t s);
 cudaError_t launch_gather_rows(const double *A, int64_t lda, int64_t N, int64_t n, const int64_t *perm,
                                double *out, cudaStream_t s);
 // gather (scatter = 0): out[k] = v[perm[k]];  scatter (1): out[perm[k]] = v[k]

@@ -530,6 +530,48 @@ cudaError_t launch_get_basis(const void *Q, int precision, int64_t n, int m, int
     return cudaGetLastError();
 }
 
+namespace {
+// acc[0] += sum_j sum_i (lam[j][i] + em lbar[j]) (x1[j][i] - x0[j][i]),
+// acc[1] += sum_j lbar[j] ((1/m) sum_i x1[j][i] - xb0[j])   (FP64 sums; [n][m] states)
+template <typename TS>
+__global__ void adj_dots_kernel(const TS *lam, const double *lbar, const TS *x1, const TS *x0, const double *xb0,
+                                int64_t n, int m, double em, double *acc) {
+    double sg = 0.0, se = 0.0;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        const double lb = lbar[j];
+        double mean = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const size_t k = size_t(j) * m + i;
+            sg += (double(lam[k]) + em * lb) * (double(x1[k]) - double(x0[k]));
+            mean += double(x1[k]);
+        }
+        se += lb * (mean / m - xb0[j]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        sg += __shfl_xor_sync(0xffffffffu, sg, off);
+        se += __shfl_xor_sync(0xffffffffu, se, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(acc, sg);
+        atomicAdd(acc + 1, se);
+    }
+}
+}  // namespace
+
+cudaError_t launch_adj_dots(const void *lam, const double *lbar, const void *x1, const void *x0, const double *xb0,
+                            int64_t n, int m, double em, int precision, double *acc, cudaStream_t s) {
+    const unsigned g = unsigned(std::min<int64_t>((n + 255) / 256, 1024));
+    if (precision == 0)
+        adj_dots_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(lam), lbar,
+                                                  static_cast<const double *>(x1), static_cast<const double *>(x0),
+                                                  xb0, n, m, em, acc);
+    else
+        adj_dots_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(lam), lbar,
+                                                 static_cast<const float *>(x1), static_cast<const float *>(x0), xb0,
+                                                 n, m, em, acc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_axpy_f64(double *y, const double *x, double a, int64_t count, cudaStream_t s) {
     axpy_kernel<<<grid1d(count, 256), 256, 0, s>>>(y, x, a, count);
     return cudaGetLastError();

@@ -320,6 +320,66 @@ def test_backward_matches_oracle_adjoint(prec, tol):
     ctx.iterate(g, e, 5)
 
 
+@pytest.mark.parametrize("prec,ck,tol", [("f64", 1, 1e-9), ("f64", 7, 1e-9), ("f64", 0, 1e-9), ("f64", 40, 1e-9),
+                                         ("f32", 0, 2e-3)])
+def test_backward_params_match_oracle(prec, ck, tol):
+    # dL/dgamma and dL/deta through T iterations, from forward states recomputed
+    # out of checkpoints every ck iterations (0 = 20; 7 leaves a short last
+    # segment), and dL/db, against the FP64 oracle sweep, for a right-hand side
+    # other than the one given at set-up (the forward trajectory depends on it)
+    apc, dev = _apc(), _dev()
+    n, m, T = 600, 6, 40
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 12)
+    b2 = np.random.default_rng(5).standard_normal(n)
+    blocks2 = O.partition(A, b2, offs)
+    xt = inputs.target_vector(n, 12)
+    xbar, _, states = O.apc_forward_linear(blocks2, Qs, Rs, g, e, T)
+    gT = xbar - xt
+    db_ref, dg_ref, de_ref = O.apc_adjoint(blocks2, Qs, Rs, g, e, T, gT, states=states)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    db, dg, de = ctx.backward_params(torch.tensor(gT, device=dev), T, g, e, b=torch.tensor(b2, device=dev),
+                                     ckpt_every=ck)
+    assert _rel(db.cpu().numpy(), np.concatenate(db_ref)) <= (1e-10 if prec == "f64" else 1e-4)
+    assert dg == pytest.approx(dg_ref, rel=tol), (dg, dg_ref)
+    assert de == pytest.approx(de_ref, rel=tol), (de, de_ref)
+    # zero iterations: no parameter dependence; the context stays usable
+    db0, dg0, de0 = ctx.backward_params(torch.tensor(gT, device=dev), 0, g, e)
+    assert dg0 == 0.0 and de0 == 0.0
+    ctx.reset()
+    ctx.iterate(g, e, 5)
+
+
+def test_backward_params_full_size_central_difference():
+    # the differentiation workload's sizes (n = 8192, m = 32 blocks of 256,
+    # T = 200, checkpoints every 20), FP64 path: dL/dgamma and dL/deta of
+    # L = 0.5 ||xbar(T) - x_target||^2 against central differences of L
+    # through the forward iteration, and the FP32 path against the FP64 one
+    apc, dev = _apc(), _dev()
+    n, m, T, g, e = 8192, 32, 200, 1.0, 1.0
+    A, _, b = inputs.gaussian_system_torch(n, 78, dev)
+    offs = inputs.even_offsets(n, m)
+    xt = torch.tensor(inputs.target_vector(n, 78), device=dev)
+    ctx = apc.apc_setup(A, b, offs, precision="f64")
+
+    def loss(gg, ee):
+        ctx.reset()
+        ctx.iterate(gg, ee, T)
+        return 0.5 * float(torch.sum((ctx.xbar() - xt) ** 2))
+
+    ctx.reset()
+    ctx.iterate(g, e, T)
+    gT = ctx.xbar() - xt
+    _, dg, de = ctx.backward_params(gT, T, g, e, ckpt_every=20)
+    h = 1e-5
+    fdg = (loss(g + h, e) - loss(g - h, e)) / (2 * h)
+    fde = (loss(g, e + h) - loss(g, e - h)) / (2 * h)
+    assert dg == pytest.approx(fdg, rel=1e-5), (dg, fdg)
+    assert de == pytest.approx(fde, rel=1e-5), (de, fde)
+    c32 = apc.apc_setup(A, b, offs, precision="f32")
+    _, dg32, de32 = c32.backward_params(gT, T, g, e, ckpt_every=20)
+    assert dg32 == pytest.approx(dg, rel=1e-3) and de32 == pytest.approx(de, rel=1e-3), (dg32, dg, de32, de)
+
+
 def test_autograd_grad_b_matches_central_difference():
     # L = 0.5 ||xbar_T - x_target||^2 is quadratic in b: central differences of the
     # FP64 oracle forward are exact up to rounding (spec bar: 1e-4 relative)
