@@ -252,42 +252,66 @@ class Context:
 
 
 class APCSolveFn:
-    """Differentiable T-iteration APC solve, xbar(T) = F(b), for torch.autograd.
+    """Differentiable T-iteration APC solve, xbar(T) = F(b, gamma, eta), for torch.autograd.
 
-    ``APCSolveFn.apply(b, ctx, gamma, eta, T)``: b is an FP64 CUDA tensor of
-    shape (N,) or (N, k) (k right-hand sides, solved one after another); the
-    backward pass returns dL/db through ``Context.backward``."""
+    ``APCSolveFn.apply(b, ctx, gamma, eta, T, ckpt_every=20)``: b is an FP64
+    CUDA tensor of shape (N,) or (N, k) (k right-hand sides, solved one after
+    another); gamma and eta are numbers or 0-d tensors.  The backward pass
+    returns dL/db through ``Context.backward``, and, when gamma or eta is a
+    tensor that requires grad, dL/dgamma and dL/deta (summed over the columns)
+    through ``Context.backward_params`` with forward checkpoints every
+    ``ckpt_every`` iterations."""
 
     _fn = None
 
     @classmethod
-    def apply(cls, b, ctx, gamma, eta, T):
+    def apply(cls, b, ctx, gamma, eta, T, ckpt_every=20):
         if cls._fn is None:
             import torch
 
             class _F(torch.autograd.Function):
                 @staticmethod
-                def forward(fctx, b, solver, gamma, eta, T):
+                def forward(fctx, b, solver, gamma, eta, T, ckpt_every):
+                    g, e = float(gamma), float(eta)
                     cols = b.unsqueeze(1) if b.dim() == 1 else b
                     outs = []
                     for j in range(cols.shape[1]):
                         solver.reset(cols[:, j].contiguous())
-                        solver.iterate(gamma, eta, T)
+                        solver.iterate(g, e, T)
                         outs.append(solver.xbar())
-                    fctx.solver, fctx.gamma, fctx.eta, fctx.T, fctx.vec = solver, gamma, eta, T, b.dim() == 1
+                    fctx.save_for_backward(b)
+                    fctx.solver, fctx.g, fctx.e, fctx.T, fctx.ck = solver, g, e, T, ckpt_every
+                    fctx.vec = b.dim() == 1
+                    fctx.like = (gamma if torch.is_tensor(gamma) else None, eta if torch.is_tensor(eta) else None)
                     x = torch.stack(outs, dim=1)
                     return x[:, 0] if b.dim() == 1 else x
 
                 @staticmethod
                 def backward(fctx, gx):
+                    (b,) = fctx.saved_tensors
+                    params = fctx.needs_input_grad[2] or fctx.needs_input_grad[3]
                     gcols = gx.unsqueeze(1) if fctx.vec else gx
-                    dbs = [fctx.solver.backward(gcols[:, j].contiguous(), fctx.T, fctx.gamma, fctx.eta)
-                           for j in range(gcols.shape[1])]
+                    bcols = b.unsqueeze(1) if fctx.vec else b
+                    dbs, dg, de = [], 0.0, 0.0
+                    for j in range(gcols.shape[1]):
+                        gj = gcols[:, j].contiguous()
+                        if params:
+                            db, dgj, dej = fctx.solver.backward_params(gj, fctx.T, fctx.g, fctx.e,
+                                                                       b=bcols[:, j].contiguous(), ckpt_every=fctx.ck)
+                            dg, de = dg + dgj, de + dej
+                        else:
+                            db = fctx.solver.backward(gj, fctx.T, fctx.g, fctx.e)
+                        dbs.append(db)
                     db = torch.stack(dbs, dim=1)
-                    return (db[:, 0] if fctx.vec else db), None, None, None, None
+                    grads = []
+                    for k, val in ((2, dg), (3, de)):
+                        ref = fctx.like[k - 2]
+                        grads.append(torch.tensor(val, dtype=ref.dtype, device=ref.device)
+                                     if fctx.needs_input_grad[k] and ref is not None else None)
+                    return (db[:, 0] if fctx.vec else db), None, grads[0], grads[1], None, None
 
             cls._fn = _F
-        return cls._fn.apply(b, ctx, gamma, eta, T)
+        return cls._fn.apply(b, ctx, gamma, eta, T, ckpt_every)
 
 
 def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:

@@ -412,6 +412,35 @@ def test_autograd_grad_b_matches_central_difference():
         assert float(np.sum(grad * d)) == pytest.approx(fd, rel=1e-4)
 
 
+def test_autograd_gamma_eta_two_columns_match_oracle():
+    # torch.autograd through APCSolveFn with gamma and eta as tensors: the
+    # gradients sum over the k = 2 columns, each from its own forward
+    # trajectory (checkpoints every 9 iterations), against the oracle
+    apc, dev = _apc(), _dev()
+    n, m, T = 400, 5, 30
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 21)
+    Bm = np.random.default_rng(6).standard_normal((n, 2))
+    Xt = np.random.default_rng(7).standard_normal((n, 2))
+    dg_ref = de_ref = 0.0
+    db_ref = []
+    for j in range(2):
+        bl = O.partition(A, Bm[:, j], offs)
+        xbar, _, states = O.apc_forward_linear(bl, Qs, Rs, g, e, T)
+        dbj, dgj, dej = O.apc_adjoint(bl, Qs, Rs, g, e, T, xbar - Xt[:, j], states=states)
+        dg_ref, de_ref = dg_ref + dgj, de_ref + dej
+        db_ref.append(np.concatenate(dbj))
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64")
+    bt = torch.tensor(Bm, device=dev, requires_grad=True)
+    gt = torch.tensor(g, dtype=torch.float64, requires_grad=True)
+    et = torch.tensor(e, dtype=torch.float64, requires_grad=True)
+    x = apc.APCSolveFn.apply(bt, ctx, gt, et, T, 9)
+    loss = 0.5 * torch.sum((x - torch.tensor(Xt, device=dev)) ** 2)
+    loss.backward()
+    assert float(gt.grad) == pytest.approx(dg_ref, rel=1e-9)
+    assert float(et.grad) == pytest.approx(de_ref, rel=1e-9)
+    assert _rel(bt.grad.cpu().numpy(), np.stack(db_ref, axis=1)) <= 1e-10
+
+
 def test_backward_tends_to_inverse_transpose_at_convergence():
     apc, dev = _apc(), _dev()
     n, m = 200, 4
