@@ -301,8 +301,10 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = kPlanesA * KP * 128;
     const uint32_t xbytes = uint32_t(KP) * (rows + kXPad) * 4;
     int pi = 0;  // next machine whose x_i tile is due
-    // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory ring
-    constexpr int kPrefetch = 4;
+    // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory
+    // ring (measured on 256 systems: 2 is 1.5 % faster than 4, 8 is 13 % slower,
+    // none 4 % slower; an L2 prefetch in sweep B made it 40 % slower)
+    constexpr int kPrefetch = 2;
     for (int w = 0; w < min(kPrefetch, nwin); ++w) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w), qbytes);
     if (!no_x)
         for (int j = 0; j < min(kPrefetch, d.m); ++j) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, j), xbytes);
