@@ -18,6 +18,8 @@ Also on the same JSON line:
                Gaussian system (2304 x 2048, 9 blocks of 256, kappa(X) ~ 1e3): the
                32768 scaled matrix has kappa(X) ~ 1e12 and needs far more
                iterations than a benchmark can run;
+  small_f64    the paper-sized FP64 case (Gaussian 500 x 500, m = 10): microseconds per
+               iteration (latency-bound: Q fits in L2) and the solve to 1e-10;
   tts_n32768   the same comparison at the headline size on a tall Gaussian
                system (36864 x 32768, 144 blocks of 256, kappa(X) ~ 1e3), with
                the spectrum estimated on the GPU (Lanczos);
@@ -313,6 +315,49 @@ def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
     return out
 
 
+def time_small_f64(dev, tol=1e-10):
+    """The paper-sized FP64 case: Gaussian 500 x 500, m = 10 blocks of 50, (gamma*, eta*) from
+    Theorem 1 with the host eigenvalues of X; Q (2 MB) sits in L2, so an iteration is bound by
+    the grid barrier and the pipeline's latency, not by HBM.  Microseconds per iteration (CUDA
+    events over 5000 iterations in one launch) and the solve to relative residual `tol`."""
+    import numpy as np
+    import torch
+    from paper_1708_01413_gb300 import apc, inputs
+    n, m = 500, 10
+    A, x_true, b = inputs.gaussian_system(n, 0)
+    offs = inputs.even_offsets(n, m)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64")
+    try:
+        X = sum(q @ q.T for q in (ctx.basis(i).cpu().numpy() for i in range(m))) / m
+        mu = np.linalg.eigvalsh(X)
+        g, e, rho = apc.apc_optimal_params(float(mu[0]), float(mu[-1]))
+        ctx.reset()
+        ctx.iterate(g, e, 200)
+        torch.cuda.synchronize()
+        e0, e1 = _ev(), _ev()
+        T = 5000
+        e0.record()
+        ctx.iterate(g, e, T)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / T
+        ctx.solve(g, e, tol=tol, max_iters=1000, check_every=1000, raise_on_error=False)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x, st = ctx.solve(g, e, tol=tol, max_iters=500000, check_every=2000, raise_on_error=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        info = ctx.info()
+        return {"workload": f"Gaussian {n} x {n}, m = {m} blocks of {n // m}, FP64", "kappa_X": float(mu[-1] / mu[0]),
+                "gamma": g, "eta": e, "rho": rho, "us_per_iter": us, "clusters": info["clusters"],
+                "solve": {"tol": tol, "seconds": dt, "iterations": st["iterations"],
+                          "rel_residual": st["rel_residual"],
+                          "rel_error": float(np.linalg.norm(x.cpu().numpy() - x_true) / np.linalg.norm(x_true)),
+                          "converged": st["rc"] == 0}}
+    finally:
+        ctx.close()
+
+
 def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
     """The FP32 path (Q in FP32) on the same matrix: iterations/s and HBM GB/s."""
     import torch
@@ -506,6 +551,10 @@ def run_ours(args):
             extra["tts_n32768"] = time_to_tolerance_large(dev)
         except Exception as exc:
             extra["tts_n32768"] = {"error": str(exc)}
+        try:
+            extra["small_f64"] = time_small_f64(dev)
+        except Exception as exc:
+            extra["small_f64"] = {"error": str(exc)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
