@@ -500,25 +500,31 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                 const int bx = g2 & (NX - 1);
                 const int li = (t - 2) * R + r;
                 if constexpr (kDF) {
-                    float2 xnew = make_float2(0.0f, 0.0f);
-                    if (lane == 0) {
-                        if (!mbar_wait(&xchg[bx], uint32_t((g2 >> NX_LOG2) & 1), a.timeout_ns)) {
-                            abort_flag = 1;
-                            abort_code = DEV_TIMEOUT_XCHG;
-                        }
-                        if (r < nrh2) {
-                            float2 Ssum = make_float2(0.0f, 0.0f);
-                            for (int kk = 0; kk < cs; ++kk) {
-                                const uint64_t w = sloc[(bx * 8 + kk) * R + r];
-                                Ssum = df_add(Ssum, make_float2(__uint_as_float(uint32_t(w)),
-                                                                __uint_as_float(uint32_t(w >> 32))));
-                            }
-                            xnew = df_add(df_mul(c_em, Ssum), df_mul(c_1e, xbf[cur * rpc + li]));
-                            xbf[(cur ^ 1) * rpc + li] = xnew;
-                        }
+                    if (lane == 0 && !mbar_wait(&xchg[bx], uint32_t((g2 >> NX_LOG2) & 1), a.timeout_ns)) {
+                        abort_flag = 1;
+                        abort_code = DEV_TIMEOUT_XCHG;
                     }
-                    xnew.x = __shfl_sync(0xffffffffu, xnew.x, 0);
-                    xnew.y = __shfl_sync(0xffffffffu, xnew.y, 0);
+                    __syncwarp();
+                    // lane kk < cs reads the row sum of cluster rank kk; a double-float
+                    // tree over lanes 0-7, then every lane takes the total and forms
+                    // xbar' itself (shorter than a serial sum in lane 0 and a broadcast:
+                    // this chain paces the step)
+                    float2 Ssum = make_float2(0.0f, 0.0f);
+                    if (lane < cs && r < nrh2) {
+                        const uint64_t w = sloc[(bx * 8 + lane) * R + r];
+                        Ssum = make_float2(__uint_as_float(uint32_t(w)), __uint_as_float(uint32_t(w >> 32)));
+                    }
+#pragma unroll
+                    for (int off = 1; off < 8; off <<= 1)
+                        Ssum = df_add(Ssum, make_float2(__shfl_xor_sync(0xffffffffu, Ssum.x, off),
+                                                        __shfl_xor_sync(0xffffffffu, Ssum.y, off)));
+                    Ssum.x = __shfl_sync(0xffffffffu, Ssum.x, 0);
+                    Ssum.y = __shfl_sync(0xffffffffu, Ssum.y, 0);
+                    float2 xnew = make_float2(0.0f, 0.0f);
+                    if (r < nrh2) {
+                        xnew = df_add(df_mul(c_em, Ssum), df_mul(c_1e, xbf[cur * rpc + li]));
+                        if (lane == 0) xbf[(cur ^ 1) * rpc + li] = xnew;
+                    }
                     const TS xh2 = xhist[((g2 & 3) * R + r) * 32 + lane];
                     const TS c = (r < nrh2 && lane < W_cta) ? TS((xnew.x - float(xh2)) + xnew.y) : TS(0);
                     coefs[((g2 & 1) * 32 + lane) * R + r] = c;
