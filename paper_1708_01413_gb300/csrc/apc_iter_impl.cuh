@@ -514,10 +514,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
                         const uint64_t w = sloc[(bx * 8 + lane) * R + r];
                         Ssum = make_float2(__uint_as_float(uint32_t(w)), __uint_as_float(uint32_t(w >> 32)));
                     }
+                    // Only the rounds the cluster size needs (2 for 4 CTAs, 1 for 2): two-row
+                    // steps gain 4-7 %.  The one-row instantiation keeps the unrolled three
+                    // rounds: with the shorter loop it measured 4 % slower.
+                    if constexpr (R == 2) {
+                        for (int off = 1; off < cs; off <<= 1)
+                            Ssum = df_add(Ssum, make_float2(__shfl_xor_sync(0xffffffffu, Ssum.x, off),
+                                                            __shfl_xor_sync(0xffffffffu, Ssum.y, off)));
+                    } else {
 #pragma unroll
-                    for (int off = 1; off < 8; off <<= 1)
-                        Ssum = df_add(Ssum, make_float2(__shfl_xor_sync(0xffffffffu, Ssum.x, off),
-                                                        __shfl_xor_sync(0xffffffffu, Ssum.y, off)));
+                        for (int off = 1; off < 8; off <<= 1)
+                            Ssum = df_add(Ssum, make_float2(__shfl_xor_sync(0xffffffffu, Ssum.x, off),
+                                                            __shfl_xor_sync(0xffffffffu, Ssum.y, off)));
+                    }
                     Ssum.x = __shfl_sync(0xffffffffu, Ssum.x, 0);
                     Ssum.y = __shfl_sync(0xffffffffu, Ssum.y, 0);
                     float2 xnew = make_float2(0.0f, 0.0f);
