@@ -1056,7 +1056,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             bfail(b, APC_ERR_CUDA, "copy of B failed");
             return bail(APC_ERR_CUDA);
         }
-        apc_options o = {APC_BF16, 0, 0, b->timeout_s};
+        apc_options o = {APC_BF16, 0, 0, b->timeout_s, 0};
         apc_ctx *c = nullptr;
         rc = apc_setup(&c, A_dev_host[sys], n, n, n, bcol, offs, m, &o, stream);
         if (rc != APC_OK) {
