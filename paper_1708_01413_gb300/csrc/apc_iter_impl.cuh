@@ -61,7 +61,6 @@ namespace iterk {
 // read before the overwrite (and one mbarrier phase per slot in flight).
 constexpr int NX_LOG2 = 3;
 constexpr int NX = 1 << NX_LOG2;
-constexpr int DELAY = 2;           // steps between a group's first and second product
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
