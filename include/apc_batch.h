@@ -97,9 +97,11 @@ int apc_batch_get_xbar(apc_batch *b, int32_t sys, double *X_dev, int64_t ldx, vo
 int apc_batch_get_x(apc_batch *b, int32_t sys, int32_t worker, double *X_dev, int64_t ldx, void *stream);
 
 /* apc_batch_set_test_hooks -- failure injection for tests, as
- * apc_set_test_hooks: every grid barrier of later launches waits for
- * grid_barrier_skew arrivals more than the grid has, and every device-side
- * wait gives up after timeout_s seconds (0 = 2 s).  A launch then returns
+ * apc_set_test_hooks: every wait of one CTA on the others' work in later
+ * launches (the grid barrier after the initialisation, and a unit's wait for
+ * the units of its system that write its inputs) waits for grid_barrier_skew
+ * arrivals more than there will be, and every device-side wait gives up
+ * after timeout_s seconds (0 = 2 s).  A launch then returns
  * APC_ERR_TIMEOUT and the batch stays usable (reset, then iterate).
  * Errors: INVALID_ARG. */
 int apc_batch_set_test_hooks(apc_batch *b, int32_t grid_barrier_skew, double timeout_s);

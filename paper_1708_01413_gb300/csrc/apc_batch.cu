@@ -12,9 +12,9 @@
 // z_i does not depend on x_i, so the second product is one GEMM per system,
 // Y = Q^T xbar, over the packed basis Q = [Q_1 .. Q_m] (n x C).
 //
-// One iteration is two sweeps separated by grid barriers, both on the 5th
-// generation tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32
-// accumulators in tensor memory), issued by one thread of a tensor-core warp:
+// One iteration is two sweeps, both on the 5th generation tensor cores
+// (tcgen05.mma, BF16 operands in shared memory, FP32 accumulators in tensor
+// memory), issued by one thread of a tensor-core warp:
 //   sweep A  unit = (system, tile of 256 rows).  The packed columns are walked
 //            in 64-column windows; for every 16-column chunk of machine i,
 //            D += Q[rows, chunk] Z[chunk, 2 planes x k] (M = 128 rows per
@@ -43,7 +43,9 @@
 // the 8 consumer warps wait on the accumulators and x_i slots and release
 // them with per-warp arrivals (every wait bounded), so no CTA-wide barrier
 // sits in the streaming loop.  The CTAs claim units at run time from one
-// counter per sweep, longest units first.
+// stream (per iteration: sweep A, then sweep B, each system-major with the
+// largest systems first); a unit waits only for the units of its own system
+// that write its inputs, so no grid-wide barrier separates the sweeps.
 //
 // Precision: Q_i is BF16 (rounded once from the FP64 QR); products accumulate
 // in FP32 in tensor memory; an operand split into planes keeps 16 (sweep
@@ -91,9 +93,9 @@ constexpr int kXSlotBytes = 32 * (kTileRows + kXPad) * 4;
 constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
 // mbarriers: Q slots full/empty, x slots full/empty, unit queue full/empty,
 // sweep-A accumulators full/free (two buffers), sweep-B accumulator full/free,
-// drain; then the unit queue and the tensor-memory address
+// drain; then the unit queue (64-bit unit indices) and the tensor-memory address
 constexpr int kNumBars = 2 * kQSlots + 2 * kXSlots + 2 * kUQ + 4 + 3;
-constexpr size_t kSmemUsed = size_t(kBarOffset) + kNumBars * sizeof(uint64_t) + (kUQ + 1) * sizeof(int);
+constexpr size_t kSmemUsed = size_t(kBarOffset) + kNumBars * sizeof(uint64_t) + kUQ * sizeof(long long) + sizeof(int);
 constexpr size_t kSmemBytes = kSmemUsed + 1024;     // slack to align the slots to 1024 bytes
 constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, sweep B: 4 x 3k
 
@@ -107,16 +109,18 @@ struct SysDesc {
     const int *coloff;       // [m + 1], multiples of 16
     float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float
     int npad, m, Cq, C;
+    int nuA, nuB;            // units of this system in sweep A and in sweep B
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo, im_hi, im_lo;
     float na_hi, na_lo, hb_hi, hb_lo;  // heavy ball: -alpha and beta
 };
 
 struct BatchArgs {
     const SysDesc *sys;
-    const int2 *unitsA;  // (system, first row of the tile), longest first
-    const int2 *unitsB;  // (system, first column), longest first
+    const int2 *unitsA;  // (system, first row of the tile), system-major, largest systems first
+    const int2 *unitsB;  // (system, first column), same order of systems
     int nA, nB;
-    uint32_t *ctr;       // [3] claim counters, one per sweep, rotating (zero at launch)
+    unsigned long long *claim;  // units claimed so far (zero at launch)
+    unsigned long long *done;   // [2 nsys] per system: sweep-A, sweep-B unit completions x 8 (zero at launch)
     int64_t iters;
     int init;
     int hb;              // 1: distributed-preconditioned heavy ball instead of APC
@@ -200,6 +204,23 @@ __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
 // (bulk copy) reads of them
 __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// x, opaque to the compiler: a stride passed through this is not hoisted out
+// of a loop as a set of per-right-hand-side offsets held in registers
+__device__ __forceinline__ uint32_t opaque_u32(uint32_t x) {
+    uint32_t y;
+    asm volatile("mov.b32 %0, %1;" : "=r"(y) : "r"(x));
+    return y;
 }
 
 // ---- arithmetic ----------------------------------------------------------------
@@ -454,14 +475,19 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
             sx = smem_u32(R.xslot(xs));
         }
         if (wact) {
-            float *xg = d.X + x_block(d.m, KP, d.npad, t, i);
+            // the x_i tile's stride, re-materialised per machine so that the
+            // compiler keeps no per-right-hand-side offsets live across machines
+            uint32_t rs;
+            asm volatile("mov.b32 %0, %1;" : "=r"(rs) : "r"(uint32_t(rows) * 4u));
+            const uint32_t sxr = sx + uint32_t(r) * 4u;
+            char *xg = reinterpret_cast<char *>(d.X + x_block(d.m, KP, d.npad, t, i) + r);
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
-                const float xo = init ? 0.0f : lds_f32(sx + (q * rows + r) * 4);
+                const float xo = init ? 0.0f : lds_f32(sxr + uint32_t(q) * rs);
                 const float v = ((xbh[q] - xo) + xbl[q]) - W[q];
                 const float xn = upd_exact(xo, gh, gl, v);
                 S[q] += xn;
-                __stcg(xg + size_t(q) * rows + r, xn);
+                __stcg(reinterpret_cast<float *>(xg + uint32_t(q) * rs), xn);
             }
         }
         if (!init) {
@@ -471,19 +497,22 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
         }
     }
     if (!wact) return;
-    float xo[KP];
+    float (&xo)[KP] = S;  // the new xbar (hi part), in place of the row sums
     if (hb) {
         // heavy ball on the preconditioned system (Sec. 4.3 update, Sec. 6):
         // W holds the gradient sum_i Q_i (Q_i^T x - c_i);
         // zeta <- beta zeta + gradient, x <- x - alpha zeta
         const float2 beta = make_float2(d.hb_hi, d.hb_lo), nalpha = make_float2(d.na_hi, d.na_lo);
+        char *xb = reinterpret_cast<char *>(d.Xb + grow), *mb = reinterpret_cast<char *>(d.Mb + grow);
+        const uint32_t ns = opaque_u32(uint32_t(d.npad) * 8u);
 #pragma unroll
         for (int q = 0; q < KP; ++q) {
-            const size_t off = size_t(q) * d.npad + grow;
-            const float2 zn = dfa(dfm(beta, __ldcg(d.Mb + off)), make_float2(W[q], 0.0f));
-            const float2 xn = dfa(__ldcg(d.Xb + off), dfm(nalpha, zn));
-            __stcg(d.Mb + off, zn);
-            __stcg(d.Xb + off, xn);
+            float2 *mq = reinterpret_cast<float2 *>(mb + size_t(q) * ns);
+            float2 *xq = reinterpret_cast<float2 *>(xb + size_t(q) * ns);
+            const float2 zn = dfa(dfm(beta, __ldcg(mq)), make_float2(W[q], 0.0f));
+            const float2 xn = dfa(__ldcg(xq), dfm(nalpha, zn));
+            __stcg(mq, zn);
+            __stcg(xq, xn);
             xo[q] = xn.x;
         }
     } else {
@@ -528,9 +557,11 @@ template <int MT>
 __device__ void store_z(const SysDesc &d, int col, const float (&Y)[16 * MT], bool zero_y) {
     constexpr int KP = 16 * MT, NA = kPlanesA * KP;
     const int lane = threadIdx.x & 31;
+    const char *ct = reinterpret_cast<const char *>(d.Ct + col);
+    const uint32_t cs = opaque_u32(uint32_t(d.Cq) * 4u);
 #pragma unroll
     for (int q = 0; q < KP; ++q) {
-        const float z = (zero_y ? 0.0f : Y[q]) - __ldg(d.Ct + size_t(q) * d.Cq + col);
+        const float z = (zero_y ? 0.0f : Y[q]) - __ldg(reinterpret_cast<const float *>(ct + size_t(q) * cs));
         const float z1 = __shfl_down_sync(0xffffffffu, z, 1);
         if ((lane & 1) == 0) {
             uint32_t w[kPlanesA];
@@ -631,6 +662,21 @@ __device__ bool grid_barrier(uint32_t *bar, uint32_t target, uint64_t timeout_ns
     return !__syncthreads_or(*reinterpret_cast<volatile int *>(abort_flag));
 }
 
+// Bounded wait until a completion counter reaches `target` (acquire); gives
+// up early when another CTA has already reported a time-out.
+__device__ bool wait_count(const unsigned long long *p, unsigned long long target, const BatchArgs &a,
+                           int *abort_flag) {
+    if (ld_acquire_u64(p) >= target) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (ld_acquire_u64(p) >= target) return true;
+        if (*reinterpret_cast<volatile int *>(a.err) != 0 || globaltimer_ns() - t0 > a.timeout_ns) break;
+    }
+    atomicExch(abort_flag, 1);
+    atomicCAS(a.err, 0, DEV_TIMEOUT_GRID);
+    return false;
+}
+
 template <int MT>
 __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -646,8 +692,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     uint64_t *dfree = dfull + 2;                          // [2] sweep-A accumulator buffer read
     uint64_t *bfull = dfree + 2, *bfree = bfull + 1;      // sweep-B accumulators ready / read
     uint64_t *drain = bfree + 1;                          // every tensor-core operation done (exit)
-    volatile int *uq = reinterpret_cast<volatile int *>(drain + 1);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1) + kUQ;
+    volatile long long *uq = reinterpret_cast<volatile long long *>(drain + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1 + kUQ);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool producer = warp == kProducerWarp, mma_warp = warp == kMmaWarp;
     const bool consumer = warp < kConsumerWarps;
@@ -689,66 +735,118 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     uint32_t uk = 0;   // units handed over so far (same count in every role)
     uint32_t mc = 0;   // sweep-A accumulations (machines) so far (tensor-core warp and consumers)
     uint32_t ubc = 0;  // sweep-B units so far (tensor-core warp and consumers)
-    uint32_t episode = 0;
     bool ok = true;
 
-    // One sweep.  The CTAs claim units from a global counter (the lists are
-    // sorted longest first, so this is list scheduling with the longest units
-    // first and the imbalance at the grid barrier is at most the shortest
-    // units).  The producer claims ahead of the other roles and hands each unit
-    // over through a small queue, so the ring keeps streaming across unit
-    // boundaries; a claim past the end hands over -1 and ends the sweep.
-    auto sweep = [&](bool is_a, uint32_t e, bool init, bool hb) {
-        const int nunits = is_a ? a.nA : a.nB;
-        const int2 *units = is_a ? a.unitsA : a.unitsB;
-        // the counter of two sweeps ago: every claim on it ended before the last grid barrier
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr[(e + 1) % 3] = 0u;
+    // The units of one launch form one stream: iteration it is the sweep-A
+    // units of every system (system-major), then the sweep-B units.  The
+    // CTAs claim from it with one counter.  The producer claims ahead of the
+    // other roles, waits until the units of the same system that write the
+    // unit's inputs are complete (sweep A of iteration it: sweep A of it - 1
+    // (x_i, xbar) and sweep B of it - 1 (z); sweep B of it: sweep A of it
+    // (xbar')), then hands the unit over through a small queue, so the ring
+    // keeps streaming across unit boundaries and across sweeps; systems are
+    // independent, so no grid-wide barrier separates the sweeps.  Every
+    // dependency lies earlier in the stream and every CTA takes its units in
+    // stream order, so the earliest incomplete unit can always proceed.  A
+    // claim past the end hands over -1 and ends the stream.
+    const long long per_it = (long long)a.nA + a.nB, total = (long long)a.iters * per_it;
+    struct Unit {
+        long long it;
+        bool is_a, init, hb;
+        int2 U;
+    };
+    auto decode = [&](long long g) {
+        Unit u;
+        u.it = g / per_it;
+        const int r = int(g - u.it * per_it);
+        u.is_a = r < a.nA;
+        u.U = u.is_a ? a.unitsA[r] : a.unitsB[r - a.nA];
+        u.init = a.init && u.it == 0;
+        u.hb = a.hb && !u.init;
+        return u;
+    };
+    auto run = [&]() {
         if (producer) {
             if (lane != 0) return;
             for (;;) {
                 const int s = int(uk % kUQ);
-                int u = -1;
+                long long g = -1;
                 if (uk < uint32_t(kUQ) || R.wait(&uqempty[s], ((uk / kUQ) - 1) & 1)) {
-                    u = int(atomicAdd(&a.ctr[e % 3], 1u));
-                    if (u >= nunits) u = -1;
+                    g = (long long)atomicAdd(a.claim, 1ull);
+                    if (g >= total) g = -1;
                 }
-                uq[s] = u;
+                Unit u = {};
+                if (g >= 0) {
+                    u = decode(g);
+                    const SysDesc &d = a.sys[u.U.x];
+                    const unsigned long long na = 8ull * unsigned(d.nuA), nb = 8ull * unsigned(d.nuB);
+                    const unsigned long long it = (unsigned long long)u.it, sk = a.barrier_skew;
+                    const unsigned long long *dn = a.done + 2 * u.U.x;
+                    const bool ready = u.is_a ? wait_count(dn, it * na + sk, a, &abort_flag) &&
+                                                    wait_count(dn + 1, it * nb + sk, a, &abort_flag)
+                                              : wait_count(dn, (it + 1) * na + sk, a, &abort_flag);
+                    if (ready) __threadfence();
+                    else g = -1;
+                }
+                uq[s] = g;
                 mbar_arrive(&uqfull[s]);
                 ++uk;
-                if (u < 0) return;
-                const int2 U = units[u];
-                if (is_a) sweep_a_producer<MT>(R, cur, a.sys[U.x], U.y, init || hb, policy);
-                else sweep_b_producer<MT>(R, cur, a.sys[U.x], U.y, policy);
+                if (g < 0) return;
+                const SysDesc &d = a.sys[u.U.x];
+                if (u.is_a) sweep_a_producer<MT>(R, cur, d, u.U.y, u.init || u.hb, policy);
+                else sweep_b_producer<MT>(R, cur, d, u.U.y, policy);
             }
         } else if (mma_warp) {
             if (lane != 0) return;
+            int prev = -1;  // sweep of the previous unit (0: A, 1: B)
             for (;;) {
                 const int s = int(uk % kUQ);
                 if (!R.wait(&uqfull[s], (uk / kUQ) & 1)) return;
-                const int u = uq[s];
+                const long long g = uq[s];
                 mbar_arrive(&uqempty[s]);
                 ++uk;
-                if (u < 0) return;
-                const int2 U = units[u];
-                if (is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, a.sys[U.x], U.y, hb, tmem);
-                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, a.sys[U.x], U.y, tmem);
+                if (g < 0) return;
+                const Unit u = decode(g);
+                const SysDesc &d = a.sys[u.U.x];
+                // sweep A's two accumulator buffers and sweep B's accumulators
+                // share tensor memory: a change of sweep waits until the
+                // consumers have read the other sweep's accumulators
+                if (u.is_a && prev == 1) {
+                    if (!R.wait(bfree, (ubc - 1) & 1)) return;
+                    tc_fence_after();
+                } else if (!u.is_a && prev == 0) {
+                    for (uint32_t j = mc >= 2 ? mc - 2 : 0; j < mc; ++j)
+                        if (!R.wait(&dfree[j & 1], (j >> 1) & 1)) return;
+                    tc_fence_after();
+                }
+                prev = u.is_a ? 0 : 1;
+                if (u.is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, d, u.U.y, u.hb, tmem);
+                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, d, u.U.y, tmem);
             }
         } else {
             for (;;) {
                 const int s = int(uk % kUQ);
                 if (!R.wait(&uqfull[s], (uk / kUQ) & 1)) return;
-                const int u = uq[s];
+                const long long g = uq[s];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&uqempty[s]);
                 ++uk;
-                if (u < 0) return;
-                const int2 U = units[u];
-                const SysDesc &d = a.sys[U.x];
-                if (is_a)
-                    sweep_a_consumer<MT>(R, cur, mc, dfull, dfree, d, U.y, init, hb, init ? 1.0f : d.g_hi,
-                                         init ? 0.0f : d.g_lo, tmem);
+                if (g < 0) return;
+                const Unit u = decode(g);
+                const SysDesc &d = a.sys[u.U.x];
+                if (u.is_a)
+                    sweep_a_consumer<MT>(R, cur, mc, dfull, dfree, d, u.U.y, u.init, u.hb, u.init ? 1.0f : d.g_hi,
+                                         u.init ? 0.0f : d.g_lo, tmem);
                 else
-                    sweep_b_consumer<MT>(R, ubc, bfull, bfree, d, U.y, tmem);
+                    sweep_b_consumer<MT>(R, ubc, bfull, bfree, d, u.U.y, tmem);
+                __syncwarp();
+                if (*reinterpret_cast<volatile int *>(&abort_flag)) return;
+                // the unit's global writes are read by other CTAs (bulk
+                // copies and loads): publish them, one arrival per warp
+                fence_proxy_async_global();
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) red_release_add_u64(a.done + 2 * u.U.x + (u.is_a ? 0 : 1), 1ull);
             }
         }
     };
@@ -769,20 +867,9 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                     }
                 }
             }
-        ++episode;
-        ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
+        ok = grid_barrier(a.bar, gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
     }
-    for (int64_t it = 0; ok && it < a.iters; ++it) {
-        const bool init = a.init && it == 0;
-        sweep(true, episode, init, a.hb && !init);
-        ++episode;
-        if (!(ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag))) break;
-        sweep(false, episode, false, false);
-        if (it + 1 < a.iters) {
-            ++episode;
-            ok = grid_barrier(a.bar, episode * gridDim.x + a.barrier_skew, a.timeout_ns, &abort_flag);
-        }
-    }
+    if (ok) run();
     // no bulk copy may still be writing this CTA's shared memory and no
     // tensor-core operation may still be using tensor memory at exit: the
     // producer waits (bounded) for the last phase of every slot it filled, the
@@ -893,7 +980,9 @@ struct apc_batch {
     std::vector<void *> owned;
     SysDesc *d_desc = nullptr;
     int2 *d_unitsA = nullptr, *d_unitsB = nullptr;
-    uint32_t *bar = nullptr;  // [4]: grid barrier counter, then the three claim counters
+    // launch counters, zeroed before every launch: [0] grid barrier (32 bit),
+    // [1] units claimed, [2 + 2 s], [3 + 2 s] completions of system s (64 bit)
+    unsigned long long *ctr = nullptr;
     int *err = nullptr;
     bool reset_done = false, params_set = false;
     int method = 0;  // 0: APC, 1: heavy ball (apc_batch_set_hb_params)
@@ -941,11 +1030,11 @@ const void *kernel_ptr(int MT) {
                    : reinterpret_cast<const void *>(&apc_batch_kernel<2>);
 }
 
-// Units sorted longest first (by bytes streamed); the CTAs claim them in this
-// order at run time.
-std::vector<int2> longest_first(std::vector<std::pair<double, int2>> items) {
-    std::stable_sort(items.begin(), items.end(),
-                     [](const std::pair<double, int2> &x, const std::pair<double, int2> &y) { return x.first > y.first; });
+// Units sorted by decreasing key, equal keys in insertion order; the CTAs
+// claim them in this order at run time.
+std::vector<int2> by_key_desc(std::vector<std::pair<double, int2>> items) {
+    using Item = std::pair<double, int2>;
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.first > y.first; });
     std::vector<int2> units;
     units.reserve(items.size());
     for (const auto &it : items) units.push_back(it.second);
@@ -959,15 +1048,16 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
     a.unitsB = b->d_unitsB;
     a.nA = b->units_a;
     a.nB = b->units_b;
-    a.ctr = b->bar + 1;
+    a.claim = b->ctr + 1;
+    a.done = b->ctr + 2;
     a.iters = iters;
     a.init = init;
     a.hb = init ? 0 : b->method;
     a.barrier_skew = b->barrier_skew;
-    a.bar = b->bar;
+    a.bar = reinterpret_cast<uint32_t *>(b->ctr);
     a.err = b->err;
     a.timeout_ns = uint64_t(b->timeout_s * 1e9);
-    BCK(b, cudaMemsetAsync(b->bar, 0, sizeof(uint32_t) * 4, s));
+    BCK(b, cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long) * (2 + 2 * size_t(b->nsys)), s));
     if (b->MT == 1)
         apc_batch_kernel<1><<<b->grid, kThreads, kSmemBytes, s>>>(a);
     else
@@ -983,7 +1073,7 @@ int check_err(apc_batch *b, cudaStream_t s) {
     if (h) {
         BCK(b, cudaMemsetAsync(b->err, 0, sizeof(int), s));
         BCK(b, cudaStreamSynchronize(s));
-        return bfail(b, APC_ERR_TIMEOUT, "a grid barrier wait ran out of time (%.3g s)", b->timeout_s);
+        return bfail(b, APC_ERR_TIMEOUT, "a wait on another CTA's work ran out of time (%.3g s)", b->timeout_s);
     }
     return APC_OK;
 }
@@ -1139,14 +1229,15 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
     }
     if (bcol) cudaFree(bcol);
     bcol = nullptr;
-    if ((rc = balloc(b, &b->d_desc, sizeof(SysDesc) * nsys)) || (rc = balloc(b, &b->bar, sizeof(uint32_t) * 4)) ||
+    if ((rc = balloc(b, &b->d_desc, sizeof(SysDesc) * nsys)) ||
+        (rc = balloc(b, &b->ctr, sizeof(unsigned long long) * (2 + 2 * size_t(nsys)))) ||
         (rc = balloc(b, &b->err, sizeof(int) * 4)))
         return bail(rc);
     if (cudaMemsetAsync(b->err, 0, sizeof(int) * 4, s) != cudaSuccess) {
         bfail(b, APC_ERR_CUDA, "memset failed");
         return bail(APC_ERR_CUDA);
     }
-    // one CTA per SM, all resident at once (the grid barriers need that)
+    // one CTA per SM, all resident at once (the CTAs wait on one another's units)
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
     if (cudaFuncSetAttribute(kernel_ptr(MT), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
@@ -1158,20 +1249,18 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         return bail(APC_ERR_LAUNCH);
     }
     b->grid = sms;
-    // work lists: cost ~ bytes streamed per unit
+    // work lists, system-major: the systems with the most bytes first, each
+    // system's units together (stable sort on the system's bytes)
     std::vector<std::pair<double, int2>> ia, ib;
     for (int sys = 0; sys < nsys; ++sys) {
-        const SysDesc &d = b->desc[sys];
-        for (int r0 = 0; r0 < d.npad; r0 += kTileRows) {
-            const int rows = std::min(kTileRows, d.npad - r0);
-            ia.push_back({double(rows) * (2.0 * d.Cq + 8.0 * d.m * kp + 64.0), make_int2(sys, r0)});
-        }
-        for (int c0 = 0; c0 < d.Cq; c0 += kColsB) {
-            const int cols = std::min(kColsB, d.Cq - c0);
-            ib.push_back({double(d.npad) * (2.0 * cols + 32.0), make_int2(sys, c0)});
-        }
+        SysDesc &d = b->desc[sys];
+        d.nuA = (d.npad + kTileRows - 1) / kTileRows;
+        d.nuB = (d.Cq + kColsB - 1) / kColsB;
+        const double bytes = double(d.npad) * (4.0 * d.Cq + 8.0 * d.m * kp);
+        for (int r0 = 0; r0 < d.npad; r0 += kTileRows) ia.push_back({bytes, make_int2(sys, r0)});
+        for (int c0 = 0; c0 < d.Cq; c0 += kColsB) ib.push_back({bytes, make_int2(sys, c0)});
     }
-    const std::vector<int2> ua = longest_first(ia), ub = longest_first(ib);
+    const std::vector<int2> ua = by_key_desc(ia), ub = by_key_desc(ib);
     b->units_a = int(ua.size());
     b->units_b = int(ub.size());
     if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * ua.size())) ||
