@@ -618,27 +618,35 @@ __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, 
     if (!R.wait(bfull, ubc & 1)) return;
     tc_fence_after();
     const uint32_t tl = tmem + (uint32_t(32 * quad) << 16);
-#pragma unroll 1
+    // both M-tiles' sums are read before the accumulators are released, so
+    // the tensor cores can start the next unit while z is formed and stored
+    float Y[2][KP];
+#pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
         const int h = (warp >> 2) + 2 * hh;
-        const int cl = 128 * h + 32 * quad;  // ncols is a multiple of 64: warp-uniform
-        if (cl >= ncols) continue;
-        float Y[KP];
+        if (128 * h + 32 * quad >= ncols) continue;  // ncols is a multiple of 64: warp-uniform
 #pragma unroll
         for (int c0 = 0; c0 < KP; c0 += 16) {
-            float p0[16], p1[16], p2[16];
-            tc_ld16(tl + uint32_t(h * NB + c0), p0);
-            tc_ld16(tl + uint32_t(h * NB + KP + c0), p1);
-            tc_ld16(tl + uint32_t(h * NB + 2 * KP + c0), p2);
+            // (plane 0 + plane 1) + plane 2, one plane's 16 columns at a time
 #pragma unroll
-            for (int j = 0; j < 16; ++j) Y[c0 + j] = (p0[j] + p1[j]) + p2[j];
+            for (int pl = 0; pl < kPlanesB; ++pl) {
+                float pv[16];
+                tc_ld16(tl + uint32_t(h * NB + pl * KP + c0), pv);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) Y[hh][c0 + j] = pl == 0 ? pv[j] : Y[hh][c0 + j] + pv[j];
+            }
         }
-        store_z<MT>(d, col0 + cl + lane, Y, false);
     }
     tc_fence_before();
     __syncwarp();
     if (lane == 0) mbar_arrive(bfree);
     ++ubc;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+        const int h = (warp >> 2) + 2 * hh;
+        const int cl = 128 * h + 32 * quad;
+        if (cl < ncols) store_z<MT>(d, col0 + cl + lane, Y[hh], false);
+    }
 }
 
 // Bounded grid barrier over all CTAs: false when the wait ran out of time.
