@@ -318,3 +318,36 @@ def test_batch_random_shapes_match_oracle(seed):
     bt.iterate(T)
     for s, ref in enumerate(refs):
         assert _rel(bt.xbar(s).cpu().numpy().reshape(ref.shape), ref) <= TOL, (s, k)
+
+
+def test_batch_results_independent_of_batch_composition():
+    # A unit computes from its own system's data only, in a fixed order, so a
+    # system's iterates are bit-identical whether it runs alone, in a batch,
+    # or in the same batch listed in reverse order.  The claim order, the
+    # CTAs that take each unit and the waits between units all change with
+    # the batch; a unit that read an input before the units writing it had
+    # completed would break the equality.
+    apc, dev = _apc(), _dev()
+    rng = np.random.default_rng(77)
+    sizes = [int(x) for x in rng.integers(17, 900, size=24)]
+    systems = _systems(sizes, 7, seed=78)
+    T = 12
+
+    def run(idx):
+        bt = apc.apc_batch_setup([torch.tensor(systems[i][0], device=dev) for i in idx],
+                                 [torch.tensor(systems[i][1], device=dev) for i in idx],
+                                 [systems[i][2] for i in idx])
+        bt.set_params([1.0] * len(idx), [1.0] * len(idx))
+        bt.reset()
+        bt.iterate(T)
+        out = {i: bt.xbar(j).cpu() for j, i in enumerate(idx)}
+        bt.close()
+        return out
+
+    fwd = run(list(range(len(systems))))
+    rev = run(list(reversed(range(len(systems)))))
+    for i in range(len(systems)):
+        assert torch.isfinite(fwd[i]).all(), i
+        assert torch.equal(fwd[i], rev[i]), i
+    for i in (0, 11, 23):
+        assert torch.equal(run([i])[i], fwd[i]), i
