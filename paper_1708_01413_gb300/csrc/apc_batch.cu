@@ -124,8 +124,8 @@ struct BatchArgs {
     int64_t iters;
     int init;
     int hb;              // 1: distributed-preconditioned heavy ball instead of APC
-    uint32_t barrier_skew;
-    uint32_t *bar;
+    uint32_t barrier_skew;  // test hook: added to every cross-CTA wait target (0 = normal)
+    uint32_t *bar;          // grid barrier after the initialisation (zero at launch)
     int *err;
     uint64_t timeout_ns;
 };
@@ -1353,7 +1353,7 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     if (!b->params_set) return bfail(b, APC_ERR_PARAMS, "apc_batch_set_params must precede apc_batch_iterate");
     if (!b->reset_done) return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_reset must precede apc_batch_iterate");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // one persistent launch (barrier reset + kernel), captured once per
+    // one persistent launch (counter reset + kernel), captured once per
     // iteration count and replayed as a CUDA graph
     if (!b->graph || b->graph_iters != iters || b->graph_method != b->method) {
         if (b->graph) {
