@@ -787,7 +787,9 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 if (g >= 0) {
                     u = decode(g);
                     const SysDesc &d = a.sys[u.U.x];
-                    const unsigned long long na = 8ull * unsigned(d.nuA), nb = 8ull * unsigned(d.nuB);
+                    // completions are counted per consumer warp: kConsumerWarps per unit
+                    const unsigned long long na = (unsigned long long)kConsumerWarps * unsigned(d.nuA);
+                    const unsigned long long nb = (unsigned long long)kConsumerWarps * unsigned(d.nuB);
                     const unsigned long long it = (unsigned long long)u.it, sk = a.barrier_skew;
                     const unsigned long long *dn = a.done + 2 * u.U.x;
                     const bool ready = u.is_a ? wait_count(dn, it * na + sk, a, &abort_flag) &&
