@@ -186,8 +186,10 @@ int apc_residual(apc_ctx *ctx, const double *x_dev, const double *rhs_dev,
  * N to 1,048,576 rows: larger N returns APC_ERR_UNSUPPORTED.  All calls share
  * that array, so calls that overlap on the GPU (different streams or host
  * threads on one device) race and may return wrong results.  The first call
- * on a device looks up the array's address with that device current; make it
- * before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, CUDA (text in
+ * on a device looks up the array's address with that device current, and so
+ * does the first call after that device's context was reset
+ * (cudaDeviceReset): the array may move when the library's code is loaded
+ * again.  Make that first call before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, CUDA (text in
  * apc_last_error(NULL)). */
 int apc_residual_noalloc(const double *A_dev, int64_t lda, int64_t N, int64_t n, const double *x_dev,
                          const double *rhs_dev, double *resid_dev, double *rel_residual_host, void *stream);

@@ -316,17 +316,32 @@ class APCSolveFn:
 
 def apc_residual_noalloc(A, x, rhs, resid_out=None, stream=None) -> float:
     """||rhs - A x|| / ||rhs|| in FP64 without any device allocation (see the
-    header): A is an N x n row-major FP64 CUDA tensor, x and rhs FP64 CUDA
-    vectors, resid_out an optional N-vector receiving rhs - A x."""
+    header): A is an N x n row-major FP64 CUDA tensor (rows may be strided, so
+    a column slice of a wider matrix is accepted), x an n-vector and rhs an
+    N-vector (FP64, contiguous), resid_out an optional contiguous N-vector
+    receiving rhs - A x.  Every tensor must be on one device; the call runs
+    with that device current.  Lengths are checked here, before anything is
+    launched, because the kernel trusts them."""
     import torch
-    for t in (A, x, rhs) + ((resid_out,) if resid_out is not None else ()):
+    ts = (A, x, rhs) + ((resid_out,) if resid_out is not None else ())
+    for t in ts:
         if not t.is_cuda or t.dtype != torch.float64:
             raise TypeError("float64 CUDA tensors expected")
-    if A.dim() != 2 or A.stride(1) != 1 or not x.is_contiguous() or not rhs.is_contiguous():
-        raise ValueError("A must be row-major; x and rhs contiguous")
+    if any(t.device != A.device for t in ts):
+        raise ValueError("A, x, rhs and resid_out must be on one device")
+    if A.dim() != 2 or A.stride(1) != 1 or A.shape[0] < 1 or A.shape[1] < 1:
+        raise ValueError("A must be a non-empty 2-D tensor with unit column stride")
+    N, n = int(A.shape[0]), int(A.shape[1])
+    if not x.is_contiguous() or x.numel() != n:
+        raise ValueError(f"x must be a contiguous vector of n = {n} values, got {tuple(x.shape)}")
+    if not rhs.is_contiguous() or rhs.numel() != N:
+        raise ValueError(f"rhs must be a contiguous vector of N = {N} values, got {tuple(rhs.shape)}")
+    if resid_out is not None and (not resid_out.is_contiguous() or resid_out.numel() != N):
+        raise ValueError(f"resid_out must be a contiguous vector of N = {N} values, got {tuple(resid_out.shape)}")
     rel = C.c_double()
-    _check(lib().apc_residual_noalloc(_ptr(A), A.stride(0), A.shape[0], A.shape[1], _ptr(x), _ptr(rhs),
-                                      _ptr(resid_out), C.byref(rel), _stream(stream)))
+    with torch.cuda.device(A.device):
+        _check(lib().apc_residual_noalloc(_ptr(A), A.stride(0), N, n, _ptr(x), _ptr(rhs), _ptr(resid_out),
+                                          C.byref(rel), _stream(stream)))
     return rel.value
 
 

@@ -16,12 +16,16 @@
 //    race on it and may return wrong results;
 //  * every entry that a call reads is first written by that same call, so no
 //    part of the array needs to start at zero;
-//  * the first call on a device looks up the array's device address
+//  * the first call on a device (and again the first call after the device's
+//    context was reset) looks up the array's device address
 //    (cudaGetSymbolAddress) with that device current; make that first call
-//    before any stream capture.
+//    before any stream capture;
+//  * every call waits for its stream to finish (the result is a host value).
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+
+#include <cuda.h>
 
 #include "../../include/apc.h"
 #include "apc_internal.h"
@@ -41,29 +45,71 @@ constexpr int64_t kMaxBlocks = 32768;
 // [0, 2*kMaxBlocks): per-block (||r||^2, ||rhs||^2); [2*kMaxBlocks, +2): totals.
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxBlocks + 2];
 
+// The array's device address, looked up once per device and context.  The
+// address belongs to the module loaded into a CUDA context; after
+// cudaDeviceReset the primary context is created anew, the module is loaded
+// again and the array may move, so the cache is keyed by the context's
+// process-unique id (cuCtxGetId), fetched through the runtime's driver entry
+// points so that the library need not link the driver library.  Where those
+// entry points are missing the address is looked up on every call.
 struct DeviceAddress {
     bool ready = false;
+    unsigned long long ctx_id = 0;
     double *ptr = nullptr;
 };
 constexpr int kMaxDevices = 64;
 DeviceAddress g_addr[kMaxDevices];
 std::mutex g_addr_mutex;
 
-// Device address of g_noalloc_scratch for the current device (looked up once).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_entry_once;
+
+// Id of the context current on this thread; false if unknown (no context yet,
+// or the driver entry points are unavailable).
+bool current_context_id(unsigned long long *id) {
+    std::call_once(g_entry_once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_noalloc_scratch for the current device and context.
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    bool have_id = current_context_id(&id);
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev].ready) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_addr[dev].ptr = static_cast<double *>(p);
-        g_addr[dev].ready = true;
+    DeviceAddress &d = g_addr[dev];
+    if (d.ready && have_id && d.ctx_id == id) {
+        *out = d.ptr;
+        return cudaSuccess;
     }
-    *out = g_addr[dev].ptr;
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (!have_id) have_id = current_context_id(&id);  // the lookup may have created the context
+    d.ptr = static_cast<double *>(p);
+    d.ctx_id = id;
+    d.ready = have_id;
+    *out = d.ptr;
     return cudaSuccess;
 }
 
