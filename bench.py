@@ -160,7 +160,9 @@ def _threads():
 
 class OracleSample:
     """The FP64 oracle's iteration on SAMPLE_BLOCKS of the workload's row
-    blocks; one step's time is scaled by m_total / SAMPLE_BLOCKS."""
+    blocks; one step's time is scaled by m_total / SAMPLE_BLOCKS (the
+    iteration's cost is linear in the number of blocks), so the figure is an
+    extrapolation to the whole workload."""
 
     def __init__(self, A_rows, p, m_total):
         import numpy as np
@@ -181,9 +183,45 @@ class OracleSample:
         self.xs, self.xbar = self.O.apc_step(self.xs, self.xbar, self.Qs, 1.0, 1.5)
         return (time.perf_counter() - t0) * self.scale
 
+    def timed(self, steps, warmup=1):
+        """Median extrapolated seconds per iteration over `steps` timed steps."""
+        for _ in range(warmup):
+            self.step_seconds()
+        return statistics.median(self.step_seconds() for _ in range(steps))
+
     def describe(self, n, p, m):
         return (f"{len(self.Qs)} of {m} row blocks ({len(self.Qs) * p} x {n} FP64) of the workload, one Eq. (cons) "
-                f"iteration per step, time scaled x{self.scale:g} to all blocks")
+                f"iteration per step, step time scaled x{self.scale:g} to all blocks (extrapolated)")
+
+
+CPU_STEPS = 10
+
+
+def single_core_rate(n, p, m):
+    """The same oracle sample timed in a child process limited to one thread
+    (BLAS and OpenMP), in iterations per second of the whole workload."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        env.pop(k, None)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker", "--n", str(n), "--m", str(m)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None
+    return float(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(A_rows, n, p, m):
+    """cpu_baseline of the JSON line: the oracle on the bounded sample with all
+    host cores and with one core."""
+    sample = OracleSample(A_rows, p, m)
+    sec = sample.timed(CPU_STEPS)
+    try:
+        single = single_core_rate(n, p, m)
+    except Exception:
+        single = None
+    return {"value": 1.0 / sec, "unit": "iter/s", "cores": _threads(), "nproc": os.cpu_count(), "kind": "oracle",
+            "single_core_value": single, "extrapolated": True, "steps": CPU_STEPS,
+            "sample": sample.describe(n, p, m)}
 
 
 def _sample_rows(n, p, seed):
@@ -210,16 +248,28 @@ def run_reference(args):
             times.append(t)
     sec = statistics.mean(times)
     value = 1.0 / sec
+    try:
+        single = single_core_rate(args.n, p, args.m)
+    except Exception:
+        single = None
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"APC n={args.n} A=D_r G D_c (log-uniform 1e-2..1e2), m={args.m} blocks of {p}"},
-        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": _threads(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": "iter/s", "cores": _threads(), "nproc": os.cpu_count(),
+                         "kind": "oracle", "single_core_value": single, "extrapolated": True,
                          "sample": sample.describe(args.n, p, args.m)},
         "e2e": {"value": value, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def run_cpu_sample_worker(args):
+    """Child process of single_core_rate: print the sample's iterations/s."""
+    p = args.n // args.m
+    sample = OracleSample(_sample_rows(args.n, p, 0), p, args.m)
+    print(1.0 / sample.timed(CPU_STEPS), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -429,8 +479,15 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
     hb1.record(stream)
     torch.cuda.synchronize()
     sec_hb = hb0.elapsed_time(hb1) / 1e3 / (reps * iters)
-    alg = 2 * info["q_bytes"] + 2 * info["state_bytes"]
+    # algorithmic bytes without the kernel's padding (rows to 32, each block's
+    # columns to 16, right-hand sides to kp): Q_s is n_s x n_s BF16 (the blocks
+    # of a square system hold n_s rows in all), x_i is n_s x k FP32 per machine
     ns = np.array([n for n, _ in specs], dtype=np.float64)
+    ms = np.array([len(o) - 1 for _, o in specs], dtype=np.float64)
+    q_alg = float((ns ** 2).sum()) * 2
+    x_alg = float((ms * ns).sum()) * k * 4
+    alg = 2 * q_alg + 2 * x_alg
+    padded = 2 * info["q_bytes"] + 2 * info["state_bytes"]
     kp = 16 if k <= 16 else 32
     cq = info["q_bytes"] / 2.0  # sum over systems of npad * Cq
     mma_flops = 2.0 * cq * kp * (2 + 3)  # both products, operands in 2 + 3 BF16 planes
@@ -442,12 +499,12 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
             "iters_per_launch": iters, "launches": reps, "setup_s": round(setup_s, 3), "grid": info["grid"],
             "clocks": clk.summary(),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "algorithmic_bytes_per_iter": alg, "kernel": "apc_batch_kernel",
-                         "tensor_tflops": mma_flops / sec / 1e12},
+                         "algorithmic_bytes_per_iter": alg, "traffic_model_padded_bytes_per_iter": padded,
+                         "kernel": "apc_batch_kernel", "tensor_tflops": mma_flops / sec / 1e12},
             "heavy_ball": {"ms_per_iter": sec_hb * 1e3, "iter_per_s": 1.0 / sec_hb,
-                           "achieved_gbs": 2 * info["q_bytes"] / sec_hb / 1e9,
-                           "frac": 2 * info["q_bytes"] / sec_hb / 1e9 / peak,
-                           "algorithmic_bytes_per_iter": 2 * info["q_bytes"]}}
+                           "achieved_gbs": 2 * q_alg / sec_hb / 1e9,
+                           "frac": 2 * q_alg / sec_hb / 1e9 / peak,
+                           "algorithmic_bytes_per_iter": 2 * q_alg}}
 
 
 def run_ours(args):
@@ -560,11 +617,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         A_s = A[:SAMPLE_BLOCKS * p].cpu().numpy()
         del A
-        sample = OracleSample(A_s, p, m)
-        secs = [sample.step_seconds() for _ in range(3)]
-        sec = statistics.mean(secs[1:])
-        cpu = {"value": 1.0 / sec, "unit": "iter/s", "cores": _threads(), "kind": "oracle",
-               "sample": sample.describe(n, p, m)}
+        cpu = cpu_baseline(A_s, n, p, m)
 
     if rank == 0:
         line = {
@@ -629,8 +682,11 @@ def main():
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--batch-iters", type=int, default=50)
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     args = p.parse_args()
-    if args.impl == "reference":
+    if args.cpu_sample_worker:
+        run_cpu_sample_worker(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         from paper_1708_01413_gb300 import build

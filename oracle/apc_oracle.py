@@ -51,7 +51,8 @@ __all__ = [
     "relative_residual", "relative_error", "invariant_drift",
     "rate_apc", "rate_cimmino", "rate_consensus", "convergence_time",
     "apc_forward_linear", "apc_adjoint", "power_mu_max", "ApcTrace",
-    "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine", "partition_rows",
+    "round_bf16", "block_coefficients", "apc_step_affine", "apc_run_affine", "apc_adjoint_affine",
+    "partition_rows",
     "precondition_blocks", "hb_optimal_params", "dhbm_step", "dhbm_run",
     "rate_dgd", "rate_dnag", "rate_dhbm", "madmm_step", "madmm_rate", "madmm_optimal_rate", "table2_row",
 ]
@@ -506,6 +507,38 @@ def apc_run_affine(Qs, cs, gamma: float, eta: float, T: int):
     for _ in range(T):
         xs, xbar = apc_step_affine(xs, xbar, Qs, cs, gamma, eta)
     return xs, xbar
+
+
+def apc_adjoint_affine(Qs, gamma: float, eta: float, T: int, g_T):
+    """Reverse-mode sweep through ``apc_run_affine``: the derivatives of a
+    loss L with respect to the block coefficients c_i, given g_T = dL/dxbar(T).
+
+    ``apc_run_affine`` is linear in (c_1..c_m): x_i(0) = Q_i c_i, xbar(0) the
+    mean, then T steps of the affine update of App. A.  Written as the plain
+    transpose of that step (P_i symmetric, Sec. 3.1), with per-machine adjoints
+    lam_i of x_i and lbar of xbar, and mu_i = lam_i(t+1) + (eta/m) lbar(t+1):
+        lam_i(t) = (1 - gamma) mu_i,
+        lbar(t)  = (1 - eta) lbar(t+1) + gamma sum_i P_i mu_i,
+        dL/dc_i += gamma Q_i^T mu_i,
+    starting from lam_i(T) = 0, lbar(T) = g_T; at t = 0 the initialisation adds
+    dL/dc_i += Q_i^T (lam_i(0) + lbar(0)/m).  With c_i = R_i^{-T} b_i
+    (``block_coefficients``) the derivative with respect to b_i is
+    R_i^{-1} dL/dc_i.  Works for n-vectors and n x k blocks.  Returns the list
+    of dL/dc_i."""
+    m = len(Qs)
+    lam = [np.zeros_like(g_T, dtype=np.float64) for _ in range(m)]
+    lbar = np.array(g_T, dtype=np.float64, copy=True)
+    dc = [np.zeros((Q.shape[1],) + np.shape(g_T)[1:]) for Q in Qs]
+    for _ in range(T):
+        mus = [lam_i + (eta / m) * lbar for lam_i in lam]
+        Pmus = [mu - Q @ (Q.T @ mu) for mu, Q in zip(mus, Qs)]
+        for i, (mu, Q) in enumerate(zip(mus, Qs)):
+            dc[i] = dc[i] + gamma * (Q.T @ mu)
+        lam = [(1.0 - gamma) * mu for mu in mus]
+        lbar = (1.0 - eta) * lbar + gamma * sum(Pmus)
+    for i, (Q, lam_i) in enumerate(zip(Qs, lam)):
+        dc[i] = dc[i] + Q.T @ (lam_i + lbar / m)
+    return dc
 
 
 # ---------------------------------------------------------------------------

@@ -102,3 +102,79 @@ def test_affine_fixed_point_on_rounded_bases_closed_form():
     x_star = np.linalg.solve(A, B)
     d = np.linalg.norm(x_fp - x_star) / np.linalg.norm(x_star)
     assert 1e-6 < d < 1e-1
+
+
+def _affine_case(n, m, seed, k=1, bf16=True):
+    A, _, B = inputs.gaussian_system(n, seed, k=k)
+    offs = inputs.even_offsets(n, m)
+    bl = O.partition(A, B, offs)
+    QR = [O.block_qr(Ai) for Ai, _ in bl]
+    Qs = [O.round_bf16(Q) if bf16 else Q for Q, _ in QR]
+    Rs = [R for _, R in QR]
+    cs = [O.block_coefficients(Q, R, bi) for (Q, R), (_, bi) in zip(QR, bl)]
+    lo, hi = O.mu_bounds([Q for Q, _ in QR])
+    g, e, _ = O.optimal_params(lo, hi)
+    return A, B, offs, bl, Qs, Rs, cs, g, e
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_affine_adjoint_matches_central_differences(k):
+    # c -> xbar(T) is linear and L = 0.5 ||xbar(T) - x_t||^2 quadratic, so a
+    # central difference in any direction equals <dL/dc, d> up to rounding
+    n, m, T = 60, 4, 25
+    A, B, offs, bl, Qs, Rs, cs, g, e = _affine_case(n, m, 41, k=k)
+    rng = np.random.default_rng(2)
+    xt = rng.standard_normal(B.shape)
+
+    def L(cc):
+        return 0.5 * float(np.sum((O.apc_run_affine(Qs, cc, g, e, T)[1] - xt) ** 2))
+
+    gT = O.apc_run_affine(Qs, cs, g, e, T)[1] - xt
+    dc = O.apc_adjoint_affine(Qs, g, e, T, gT)
+    for _ in range(3):
+        d = [rng.standard_normal(c.shape) for c in cs]
+        h = 0.3
+        fd = (L([c + h * di for c, di in zip(cs, d)]) - L([c - h * di for c, di in zip(cs, d)])) / (2 * h)
+        an = sum(float(np.sum(a * di)) for a, di in zip(dc, d))
+        assert an == pytest.approx(fd, rel=1e-9)
+
+
+def test_affine_adjoint_dot_product_test():
+    # <J v, w> = <v, J^T w> for the linear map J: (c_i) -> xbar(T)
+    n, m, T = 50, 5, 30
+    A, B, offs, bl, Qs, Rs, cs, g, e = _affine_case(n, m, 42)
+    rng = np.random.default_rng(3)
+    v = [rng.standard_normal(c.shape) for c in cs]
+    w = rng.standard_normal(n)
+    Jv = O.apc_run_affine(Qs, v, g, e, T)[1]
+    JTw = O.apc_adjoint_affine(Qs, g, e, T, w)
+    lhs, rhs = float(Jv @ w), sum(float(a @ b) for a, b in zip(v, JTw))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), abs(rhs))
+
+
+def test_affine_adjoint_equals_cons_adjoint_for_orthonormal_bases():
+    # with exact (orthonormal) bases both forms give one map b -> xbar(T), so
+    # R_i^{-1} dL/dc_i equals the Eq. (cons) sweep's dL/db_i (a different
+    # recursion: per-machine lam_i carry Q_i Q_i^T terms there)
+    import scipy.linalg as sla
+    n, m, T = 48, 4, 20
+    A, B, offs, bl, Qs, Rs, cs, g, e = _affine_case(n, m, 43, bf16=False)
+    gT = np.random.default_rng(4).standard_normal(n)
+    dc = O.apc_adjoint_affine(Qs, g, e, T, gT)
+    db_aff = np.concatenate([sla.solve_triangular(R, d, lower=False) for R, d in zip(Rs, dc)])
+    db_cons = np.concatenate(O.apc_adjoint(bl, Qs, Rs, g, e, T, gT)[0])
+    assert np.linalg.norm(db_aff - db_cons) <= 1e-10 * np.linalg.norm(db_cons)
+
+
+def test_affine_adjoint_tends_to_the_fixed_point_adjoint():
+    # the affine iteration converges to x* = M^{-1} sum_i Q_i c_i with
+    # M = sum_i Q_i Q_i^T (rounded bases included), so for many iterations
+    # dL/dc_i tends to Q_i^T M^{-1} g (closed form, numpy.linalg.solve)
+    n, m = 40, 4
+    A, B, offs, bl, Qs, Rs, cs, g, e = _affine_case(n, m, 44)
+    gT = np.random.default_rng(5).standard_normal(n)
+    M = sum(Q @ Q.T for Q in Qs)
+    want = [Q.T @ np.linalg.solve(M, gT) for Q in Qs]
+    dc = O.apc_adjoint_affine(Qs, g, e, 3000, gT)
+    err = max(np.linalg.norm(a - b) / np.linalg.norm(b) for a, b in zip(dc, want))
+    assert err <= 1e-9
