@@ -61,7 +61,8 @@ def test_noalloc_residual_chunk_boundaries_strided_rows_and_no_vector(n):
     # residual vector requested; checked against the context-based residual
     # and against the plain definition, on two calls in a row
     apc, dev = _env()
-    N, m, extra = n + 40, 8, 24
+    N, extra = n + 40, 24
+    m = (N + 199) // 200  # blocks of at most 200 rows
     A, _, b = inputs.gaussian_system(n, 22, N=N)
     wide = np.concatenate([A, np.random.default_rng(1).standard_normal((N, extra))], axis=1)
     Aw = torch.tensor(wide, device=dev)[:, :n]
