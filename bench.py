@@ -326,8 +326,10 @@ def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
     against FP32 + FP64 refinement, plus the residual plain FP32 reaches in a
     bounded run.  Each context estimates the extreme eigenvalues of its own X
     with the GPU Lanczos (apc_spectral_bounds), margins 0.98 / 1.01, then
-    Theorem 1's (gamma, eta).  `seconds` covers the solve alone (set-up and
-    Lanczos are reported beside it)."""
+    Theorem 1's (gamma, eta).  `seconds` covers the solve alone; set-up and
+    Lanczos are reported beside it, and `total_s` is the user-visible time to
+    the tolerance: set-up + Lanczos + solve.  FP32 checks its inner solves with
+    the free residual monitor, BF16 with FP64 residuals (counts beside)."""
     import torch
     from paper_1708_01413_gb300 import apc, inputs
     m = N // p
@@ -357,7 +359,9 @@ def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
                         "rel_residual": st["rel_residual"],
                         "rel_error": float(torch.linalg.norm(x - x_true) / torch.linalg.norm(x_true)),
                         "converged": st["rc"] == 0, "mu_bounds": [lo, hi], "kappa_X": hi / lo, "rho": rho,
-                        "setup_s": round(t_setup, 3), "lanczos_s": round(t_lanczos, 3)}
+                        "setup_s": round(t_setup, 3), "lanczos_s": round(t_lanczos, 3),
+                        "total_s": round(t_setup + t_lanczos + dt, 3),
+                        "residual_checks": st["residual_checks"], "monitor_checks": st["monitor_checks"]}
         finally:
             ctx.close()
     del A, b
@@ -507,6 +511,65 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
                            "algorithmic_bytes_per_iter": 2 * q_alg}}
 
 
+def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3):
+    """The differentiation workload: A n x n Gaussian, m blocks, k right-hand
+    sides, T iterations forward (xbar(T) for all k columns) and the reverse
+    sweep back to dL/dB, each one call (apc_forward_rhs / apc_backward_rhs).
+    BF16 context: the k columns together on the tensor cores (App. A form);
+    FP32 context: column after column through the iteration kernel.
+    Algorithmic bytes per tensor-core iteration: the packed BF16 basis read
+    twice (one product each, n x n x 2 bytes unpadded) plus the machines'
+    iterates read and written (forward only: m n k x 4 bytes twice); the
+    reverse sweep has no per-machine state (every machine's adjoint is one
+    shared vector), only its n x k row state (double-float ell and lbar, read
+    and written: 32 n k bytes)."""
+    import torch
+    from paper_1708_01413_gb300 import apc, inputs
+    A, _, _ = inputs.gaussian_system_torch(n, 77, dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(78)
+    B = torch.randn((n, k), generator=gen, device=dev, dtype=torch.float64)
+    G = torch.randn((n, k), generator=gen, device=dev, dtype=torch.float64)
+    offs = inputs.even_offsets(n, m)
+    gam, eta = 1.0, 1.5
+    out = {"workload": f"Gaussian {n} x {n}, m = {m} blocks of {n // m}, k = {k}, T = {T}"}
+    for prec in ("bf16", "f32"):
+        ctx = apc.apc_setup(A, B[:, 0].contiguous(), offs, precision=prec)
+        try:
+            X = ctx.forward_rhs(B, T, gam, eta)  # warm-up (builds the tensor-core batch on BF16)
+            ctx.backward_rhs(G, T, gam, eta)
+            torch.cuda.synchronize()
+            f0, f1, b1 = _ev(), _ev(), _ev()
+            f0.record(stream)
+            for _ in range(reps):
+                ctx.forward_rhs(B, T, gam, eta, out=X)
+            f1.record(stream)
+            for _ in range(reps):
+                ctx.backward_rhs(G, T, gam, eta)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            fwd = f0.elapsed_time(f1) / reps / 1e3
+            bwd = f1.elapsed_time(b1) / reps / 1e3
+            r = {"forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "total_ms": (fwd + bwd) * 1e3}
+            if prec == "bf16":
+                q = 2.0 * n * n
+                fb, bb = 2 * q + 2 * m * n * k * 4, 2 * q + 32 * n * k
+                r.update({"path": "tensor cores (tcgen05), k columns together",
+                          "forward_gbs": fb * T / fwd / 1e9, "forward_frac": fb * T / fwd / 1e9 / peak,
+                          "backward_gbs": bb * T / bwd / 1e9, "backward_frac": bb * T / bwd / 1e9 / peak,
+                          "bytes_per_iter_forward": fb, "bytes_per_step_backward": bb,
+                          "q_reads_per_iter": 2})
+            else:
+                r.update({"path": "iteration kernel, one column after another",
+                          "q_reads_per_iter": k})
+            out[prec] = r
+        finally:
+            ctx.close()
+    del A
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -599,6 +662,11 @@ def run_ours(args):
             extra["batch"] = time_batch(dev, peak, stream)
         except Exception as exc:
             extra["batch"] = {"error": str(exc)}
+    if args.rhs and rank == 0:
+        try:
+            extra["rhs"] = time_rhs(dev, peak, stream)
+        except Exception as exc:
+            extra["rhs"] = {"error": str(exc)}
     if args.tts and rank == 0:
         try:
             extra["tts"] = time_to_tolerance(dev)
@@ -677,6 +745,7 @@ def main():
     p.add_argument("--tts", type=int, default=1, help="also measure time to 1e-10 (BF16+IR vs FP32+IR)")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--batch", type=int, default=1, help="also time the batched solver (256 systems, k = 32)")
+    p.add_argument("--rhs", type=int, default=1, help="also time the differentiation workload (k = 16, T = 200)")
     p.add_argument("--only", default="all", choices=["all", "batch"],
                    help="batch: time only the batched workload (for profiling)")
     p.add_argument("--batch-systems", type=int, default=256)

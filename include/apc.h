@@ -69,6 +69,8 @@ typedef struct apc_stats {
     int32_t sweeps;         /* refinement sweeps (1 without refinement)       */
     double  rel_residual;   /* final ||b - A x||_2 / ||b||_2, FP64            */
     double  seconds;        /* wall time of the solve on the host clock       */
+    int64_t residual_checks; /* FP64 residuals ||b - A x|| computed (one sweep over A each) */
+    int64_t monitor_checks;  /* free monitor checks (apc_monitor), FP32/FP64 contexts */
 } apc_stats;
 
 /* apc_setup -- partition [A, b] into m row blocks and factor each block.
@@ -194,14 +196,33 @@ int apc_residual(apc_ctx *ctx, const double *x_dev, const double *rhs_dev,
 int apc_residual_noalloc(const double *A_dev, int64_t lda, int64_t N, int64_t n, const double *x_dev,
                          const double *rhs_dev, double *resid_dev, double *rel_residual_host, void *stream);
 
+/* apc_monitor -- the free residual monitor: an estimate of
+ * ||r - A xbar||_2 / ||r||_2 for the current xbar and the right-hand side r of
+ * the last apc_reset, without reading A.  Block i's residual is
+ * A_i xbar - r_i = D_i^{-1} R_i'^T (Q_i^T xbar - c_i), with (D_i A_i)^T = Q_i R_i'
+ * (row scaling D_i, two Cholesky factors) and c_i = R_i'^{-T} D_i r_i; because
+ * every x_i solves A_i x = r_i (the invariant of App. A),
+ * Q_i^T xbar - c_i = Q_i^T (xbar - x_i) = z_i, the coefficients the iteration
+ * kernel already holds for its next pass.  So the estimate costs a p_i x p_i
+ * product per block.  Its error is set by the precision of the stored bases
+ * and of z: about 1e-6 of ||r|| with FP32 bases, 1e-13 with FP64, and near
+ * 4e-3 with BF16 bases (their rounding moves Q_i^T xbar by that much).
+ * Synchronises `stream`.  Errors: INVALID_ARG (no forward state: call
+ * apc_reset first), CUDA. */
+int apc_monitor(apc_ctx *ctx, double *rel_residual_host, void *stream);
+
 /* apc_solve -- run Algorithm 1 from the least-norm initialisation until the
  * FP64 relative residual ||b - A xbar|| / ||b|| <= tol, checking every
- * `check_every` iterations, or max_iters iterations.  With refine != 0 the
- * iteration runs as the inner solver of FP64 iterative refinement:
+ * `check_every` iterations, or max_iters iterations.  FP32 and FP64 contexts
+ * check with the free monitor (apc_monitor) and compute the FP64 residual
+ * (a sweep over A) only when the monitor reaches tol, every eighth check and
+ * at the end; BF16 contexts check with the FP64 residual.  With refine != 0
+ * the iteration runs as the inner solver of FP64 iterative refinement:
  * x <- x + delta, where delta is the APC solution of A delta = b - A x,
- * stopped when its residual stagnates.  The solution (FP64, n) goes to
- * x_dev.  Errors: NOT_CONVERGED (x_dev still holds the last iterate),
- * DIVERGED, PARAMS, TIMEOUT, CUDA. */
+ * stopped when its residual (monitor, or FP64 for BF16) is below 1e-4 of
+ * ||b - A x|| or stagnates; one FP64 residual per sweep.  The solution (FP64,
+ * n) goes to x_dev.  Errors: NOT_CONVERGED (x_dev still holds the last
+ * iterate), DIVERGED, PARAMS, TIMEOUT, CUDA. */
 int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_iters,
               int64_t check_every, int32_t refine, double *x_dev, apc_stats *stats,
               void *stream);
@@ -241,6 +262,64 @@ int apc_backward(apc_ctx *ctx, const double *g_dev, int64_t T, double gamma, dou
 int apc_backward_params(apc_ctx *ctx, const double *g_dev, const double *b_dev, int64_t T, double gamma,
                         double eta, int32_t ckpt_every, double *db_dev, double *dgamma_host, double *deta_host,
                         void *stream);
+
+/* apc_forward_rhs -- the forward map of apc_backward for k right-hand sides
+ * in one call: for each column b_j of B (N x k FP64, row-major, leading
+ * dimension ldb >= k, caller's row order; device), x_i(0) the least-norm
+ * solution of block i, xbar(0) their mean, then T iterations with
+ * (gamma, eta); xbar_j(T) goes to column j of X (n x k FP64, ldx >= k;
+ * device).  Eq. (cons) is column-wise (Sec. 3.1, Algorithm 1), so the columns
+ * share every read of the bases:
+ *   - BF16 context of a square system with contiguous blocks and 2 <= k <= 32:
+ *     the k columns run together on the tensor cores in the form of App. A,
+ *     z_i = Q_i^T xbar - c_i, x_i <- x_i + gamma (xbar - x_i - Q_i z_i) (equal to
+ *     Eq. (cons) in exact arithmetic; see apc_batch.h), one persistent launch
+ *     for the T iterations, on a one-system batch that the context builds on
+ *     the first such call (set-up cost and memory of apc_batch_setup; rebuilt
+ *     when k changes; it also uses the iteration state);
+ *   - any other context: the columns one after another through the
+ *     iteration kernel (apc_reset, apc_iterate), in this one call.
+ * Uses the context's iteration state (a later apc_iterate needs apc_reset).
+ * Errors: PARAMS (gamma outside (0, 2)), INVALID_ARG, NOMEM, TIMEOUT, CUDA. */
+int apc_forward_rhs(apc_ctx *ctx, const double *B_dev, int64_t k, int64_t ldb, int64_t T, double gamma, double eta,
+                    double *X_dev, int64_t ldx, void *stream);
+
+/* apc_backward_rhs -- apc_backward for k columns in one call: G_dev holds
+ * dL/dxbar_j(T) (n x k FP64, ldg >= k; device) and DB_dev receives dL/dB
+ * (N x k FP64, lddb >= k, caller's row order; device) for the map of
+ * apc_forward_rhs with the same context, T, gamma and eta.  On the tensor-core
+ * form the sweep is the exact transpose of that form's steps (every machine's
+ * adjoint is one shared vector there, so a step is two GEMMs over the packed
+ * bases, like the forward), one persistent launch for the T steps; otherwise
+ * the columns go one after another through apc_backward.  Uses the context's
+ * iteration state.  Errors: as apc_forward_rhs. */
+int apc_backward_rhs(apc_ctx *ctx, const double *G_dev, int64_t k, int64_t ldg, int64_t T, double gamma, double eta,
+                     double *DB_dev, int64_t lddb, void *stream);
+
+/* apc_set_deterministic -- with on != 0, later launches of the iteration
+ * kernel sum the clusters' partial products z_i' = sum_j Q_i[j,:]^T (...) in a
+ * fixed order (each cluster stores its partial; after a grid-wide barrier
+ * the partials are added cluster by cluster) instead of with floating-point
+ * atomics, whose order varies from run to run.  A context's trajectory is
+ * then the same bit for bit on every run with the same launch configuration,
+ * at the cost of one more grid-wide barrier per iteration and a buffer of
+ * clusters x m x width values (allocated on the first call).  on = 0 returns
+ * to atomics.  Errors: INVALID_ARG, NOMEM. */
+int apc_set_deterministic(apc_ctx *ctx, int32_t on);
+
+/* apc_state_bytes / apc_export_state / apc_import_state -- checkpoint and
+ * resume of the iteration state: the machines' iterates x_i, xbar, the
+ * coefficients z of the next pass (all three rotating buffers), the pass
+ * counter and ||r||^2 of the last reset, behind a header that records the
+ * problem's shape and precision.  apc_state_bytes gives the size of the host
+ * buffer; export copies the state into it (synchronises `stream`); import
+ * loads a state exported from a context of the same shape (n, N, m, block
+ * width) and precision, and a later apc_iterate continues from it exactly
+ * where the exporting context stood (bit for bit in deterministic mode).
+ * Errors: INVALID_ARG (buffer too short, another shape, not a state), CUDA. */
+int apc_state_bytes(const apc_ctx *ctx, size_t *bytes);
+int apc_export_state(apc_ctx *ctx, void *host_buf, size_t bytes, void *stream);
+int apc_import_state(apc_ctx *ctx, const void *host_buf, size_t bytes, void *stream);
 
 /* apc_set_test_hooks -- failure injection for tests, on the host side of a
  * device wait: every grid barrier of later launches waits for

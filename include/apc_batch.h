@@ -89,6 +89,32 @@ int apc_batch_reset(apc_batch *b, const double *const *B_dev_host, void *stream)
  * TIMEOUT, CUDA. */
 int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream);
 
+/* apc_batch_forward -- apc_batch_reset with B_dev_host (or the stored
+ * right-hand sides when NULL), T iterations, and each system's xbar(T) into
+ * X_dev_host[s] (n_s x k FP64, leading dimension k; device), in one call.
+ * Errors: as apc_batch_reset and apc_batch_iterate (PARAMS also when the
+ * batch is set to heavy ball). */
+int apc_batch_forward(apc_batch *b, const double *const *B_dev_host, int64_t T, double *const *X_dev_host,
+                      void *stream);
+
+/* apc_batch_backward -- reverse-mode sweep through the map of
+ * apc_batch_forward, B_s -> xbar_s(T), for every system at once: given
+ * G_dev_host[s] = dL/dxbar_s(T) (n_s x k FP64, leading dimension k; device)
+ * it writes dL/dB_s to DB_dev_host[s] (same layout).  The map is linear.  Its
+ * step (App. A form above) transposes, with lam_i the adjoint of x_i and lbar
+ * that of xbar, mu_i = lam_i + (eta/m) lbar, to
+ *     lam_i <- (1 - gamma) mu_i,  lbar <- (1 - eta) lbar + gamma sum_i P_i mu_i,
+ *     dL/dc_i += gamma Q_i^T mu_i,
+ * from lam_i = 0, lbar = G; all lam_i stay equal (one vector ell), so a step
+ * is v = Q^T mu over the packed basis (sweep B) and sum_i Q_i v_i (sweep A),
+ * both on the tensor cores, in one persistent launch for the T steps.  The
+ * initialisation adds dL/dc_i += Q_i^T (ell + lbar/m), and
+ * dL/db_i = R_i^{-1} dL/dc_i (c_i = R_i^{-T} b_i).  Uses the iteration state
+ * (a later apc_batch_iterate needs apc_batch_reset).  Errors: PARAMS (no APC
+ * parameters set, or heavy ball), INVALID_ARG, NOMEM, TIMEOUT, CUDA. */
+int apc_batch_backward(apc_batch *b, const double *const *G_dev_host, int64_t T, double *const *DB_dev_host,
+                       void *stream);
+
 /* apc_batch_get_xbar -- the master's estimate of system s as FP64,
  * n_s x k row-major with leading dimension ldx >= k, into X_dev.
  * apc_batch_get_x -- the iterate x_i of machine `worker` of system s, same

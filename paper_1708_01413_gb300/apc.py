@@ -29,6 +29,8 @@ EXPORTED = (
     "apc_spectral_bounds", "apc_setup_rows", "apc_hb_optimal_params", "apc_batch_set_hb_params",
     "apc_batch_setup", "apc_batch_set_params", "apc_batch_reset", "apc_batch_iterate", "apc_batch_get_xbar",
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
+    "apc_residual_noalloc", "apc_forward_rhs", "apc_backward_rhs", "apc_batch_forward", "apc_batch_backward",
+    "apc_monitor", "apc_set_deterministic", "apc_state_bytes", "apc_export_state", "apc_import_state",
 )
 
 
@@ -46,7 +48,7 @@ class apc_options(C.Structure):
 
 class apc_stats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("sweeps", C.c_int32), ("rel_residual", C.c_double),
-                ("seconds", C.c_double)]
+                ("seconds", C.c_double), ("residual_checks", C.c_int64), ("monitor_checks", C.c_int64)]
 
 
 _lib = None
@@ -80,7 +82,15 @@ def lib() -> C.CDLL:
     L.apc_set_test_hooks.argtypes = [vp, i32, dbl]
     L.apc_spectral_bounds.argtypes = [vp, i32, C.c_uint64, C.POINTER(dbl), C.POINTER(dbl), vp]
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
-    L.apc_residual_noalloc.restype = C.c_int
+    L.apc_forward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
+    L.apc_monitor.argtypes = [vp, C.POINTER(dbl), vp]
+    L.apc_set_deterministic.argtypes = [vp, i32]
+    L.apc_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
+    L.apc_export_state.argtypes = [vp, vp, C.c_size_t, vp]
+    L.apc_import_state.argtypes = [vp, vp, C.c_size_t, vp]
+    L.apc_backward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
+    L.apc_batch_forward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
+    L.apc_batch_backward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
     L.apc_last_error.argtypes = [vp]
     L.apc_last_error.restype = C.c_char_p
     L.apc_destroy.argtypes = [vp]
@@ -200,6 +210,31 @@ class Context:
                                   _stream(stream)), self.handle)
         return rel.value
 
+    def set_deterministic(self, on: bool = True):
+        """Fixed-order reduction of the clusters' partial sums (bit-for-bit
+        reproducible trajectories; apc_set_deterministic)."""
+        _check(lib().apc_set_deterministic(self.handle, int(bool(on))), self.handle)
+
+    def export_state(self, stream=None) -> bytes:
+        """The iteration state (x_i, xbar, z buffers, pass counter) as bytes."""
+        size = C.c_size_t()
+        _check(lib().apc_state_bytes(self.handle, C.byref(size)), self.handle)
+        buf = C.create_string_buffer(size.value)
+        _check(lib().apc_export_state(self.handle, buf, size.value, _stream(stream)), self.handle)
+        return buf.raw
+
+    def import_state(self, state: bytes, stream=None):
+        """Load a state from export_state of a context of the same shape."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(lib().apc_import_state(self.handle, buf, len(state), _stream(stream)), self.handle)
+
+    def monitor(self, stream=None) -> float:
+        """The free residual monitor ||r - A xbar|| / ||r|| of the current
+        state (apc_monitor), without reading A."""
+        rel = C.c_double()
+        _check(lib().apc_monitor(self.handle, C.byref(rel), _stream(stream)), self.handle)
+        return rel.value
+
     def spectral_bounds(self, steps: int = 100, seed: int = 1, stream=None):
         """Lanczos estimates (mu_min, mu_max) of the extreme eigenvalues of X
         (Ritz values: inside the spectrum)."""
@@ -236,6 +271,41 @@ class Context:
                                          _stream(stream)), self.handle)
         return out, dg.value, de.value
 
+    def _rhs_matrix(self, B, rows):
+        import torch
+        if not B.is_cuda or B.dtype != torch.float64:
+            raise TypeError("float64 CUDA tensors expected")
+        B = B.unsqueeze(1) if B.dim() == 1 else B
+        if B.dim() != 2 or B.shape[0] != rows or B.stride(1) != 1:
+            raise ValueError(f"expected a row-major ({rows}, k) tensor, got {tuple(B.shape)}")
+        return B
+
+    def forward_rhs(self, B, T: int, gamma: float, eta: float, out=None, stream=None):
+        """xbar(T) for every column of B (N x k) from the least-norm start, in
+        one call (apc_forward_rhs); returns an n x k FP64 tensor."""
+        import torch
+        inf = self.info()
+        B = self._rhs_matrix(B, inf["N"])
+        k = B.shape[1]
+        out = torch.empty((inf["n"], k), dtype=torch.float64, device=self.device) if out is None else out
+        with torch.cuda.device(self.device):
+            _check(lib().apc_forward_rhs(self.handle, _ptr(B), k, B.stride(0), int(T), float(gamma), float(eta),
+                                         _ptr(out), out.stride(0), _stream(stream)), self.handle)
+        return out
+
+    def backward_rhs(self, G, T: int, gamma: float, eta: float, out=None, stream=None):
+        """dL/dB (N x k) from G = dL/dxbar(T) (n x k) through the map of
+        forward_rhs, in one call (apc_backward_rhs)."""
+        import torch
+        inf = self.info()
+        G = self._rhs_matrix(G, inf["n"])
+        k = G.shape[1]
+        out = torch.empty((inf["N"], k), dtype=torch.float64, device=self.device) if out is None else out
+        with torch.cuda.device(self.device):
+            _check(lib().apc_backward_rhs(self.handle, _ptr(G), k, G.stride(0), int(T), float(gamma), float(eta),
+                                          _ptr(out), out.stride(0), _stream(stream)), self.handle)
+        return out
+
     def solve(self, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False,
               out=None, stream=None, raise_on_error=True):
         import torch
@@ -245,7 +315,7 @@ class Context:
         rc = lib().apc_solve(self.handle, gamma, eta, tol, int(max_iters), int(check_every), int(bool(refine)),
                              _ptr(out), C.byref(st), _stream(stream))
         stats = dict(iterations=st.iterations, sweeps=st.sweeps, rel_residual=st.rel_residual,
-                     seconds=st.seconds, rc=rc)
+                     seconds=st.seconds, residual_checks=st.residual_checks, monitor_checks=st.monitor_checks, rc=rc)
         if rc != 0 and raise_on_error:
             _check(rc, self.handle)
         return out, stats
@@ -255,12 +325,16 @@ class APCSolveFn:
     """Differentiable T-iteration APC solve, xbar(T) = F(b, gamma, eta), for torch.autograd.
 
     ``APCSolveFn.apply(b, ctx, gamma, eta, T, ckpt_every=20)``: b is an FP64
-    CUDA tensor of shape (N,) or (N, k) (k right-hand sides, solved one after
-    another); gamma and eta are numbers or 0-d tensors.  The backward pass
-    returns dL/db through ``Context.backward``, and, when gamma or eta is a
-    tensor that requires grad, dL/dgamma and dL/deta (summed over the columns)
-    through ``Context.backward_params`` with forward checkpoints every
-    ``ckpt_every`` iterations."""
+    CUDA tensor of shape (N,) or (N, k); gamma and eta are numbers or 0-d
+    tensors.  With only b differentiated, each direction is one call into the
+    library for all k columns: ``Context.forward_rhs`` and
+    ``Context.backward_rhs`` (on a BF16 context of a square system with
+    2 <= k <= 32 the columns run together on the tensor cores in the form of
+    App. A; otherwise column after column inside the call).  When gamma or eta
+    is a tensor that requires grad, the columns go one after another through
+    the single-system iteration, and dL/dgamma, dL/deta (summed over the
+    columns) come from ``Context.backward_params`` with forward checkpoints
+    every ``ckpt_every`` iterations."""
 
     _fn = None
 
@@ -273,36 +347,40 @@ class APCSolveFn:
                 @staticmethod
                 def forward(fctx, b, solver, gamma, eta, T, ckpt_every):
                     g, e = float(gamma), float(eta)
+                    params = any(torch.is_tensor(p) and p.requires_grad for p in (gamma, eta))
                     cols = b.unsqueeze(1) if b.dim() == 1 else b
-                    outs = []
-                    for j in range(cols.shape[1]):
-                        solver.reset(cols[:, j].contiguous())
-                        solver.iterate(g, e, T)
-                        outs.append(solver.xbar())
+                    if params:
+                        outs = []
+                        for j in range(cols.shape[1]):
+                            solver.reset(cols[:, j].contiguous())
+                            solver.iterate(g, e, T)
+                            outs.append(solver.xbar())
+                        x = torch.stack(outs, dim=1)
+                    else:
+                        x = solver.forward_rhs(cols.contiguous(), T, g, e)
                     fctx.save_for_backward(b)
                     fctx.solver, fctx.g, fctx.e, fctx.T, fctx.ck = solver, g, e, T, ckpt_every
-                    fctx.vec = b.dim() == 1
+                    fctx.vec, fctx.params = b.dim() == 1, params
                     fctx.like = (gamma if torch.is_tensor(gamma) else None, eta if torch.is_tensor(eta) else None)
-                    x = torch.stack(outs, dim=1)
                     return x[:, 0] if b.dim() == 1 else x
 
                 @staticmethod
                 def backward(fctx, gx):
                     (b,) = fctx.saved_tensors
-                    params = fctx.needs_input_grad[2] or fctx.needs_input_grad[3]
                     gcols = gx.unsqueeze(1) if fctx.vec else gx
                     bcols = b.unsqueeze(1) if fctx.vec else b
-                    dbs, dg, de = [], 0.0, 0.0
-                    for j in range(gcols.shape[1]):
-                        gj = gcols[:, j].contiguous()
-                        if params:
-                            db, dgj, dej = fctx.solver.backward_params(gj, fctx.T, fctx.g, fctx.e,
-                                                                       b=bcols[:, j].contiguous(), ckpt_every=fctx.ck)
+                    dg = de = 0.0
+                    if fctx.params:
+                        dbs = []
+                        for j in range(gcols.shape[1]):
+                            db, dgj, dej = fctx.solver.backward_params(gcols[:, j].contiguous(), fctx.T, fctx.g,
+                                                                       fctx.e, b=bcols[:, j].contiguous(),
+                                                                       ckpt_every=fctx.ck)
                             dg, de = dg + dgj, de + dej
-                        else:
-                            db = fctx.solver.backward(gj, fctx.T, fctx.g, fctx.e)
-                        dbs.append(db)
-                    db = torch.stack(dbs, dim=1)
+                            dbs.append(db)
+                        db = torch.stack(dbs, dim=1)
+                    else:
+                        db = fctx.solver.backward_rhs(gcols.contiguous(), fctx.T, fctx.g, fctx.e)
                     grads = []
                     for k, val in ((2, dg), (3, de)):
                         ref = fctx.like[k - 2]
@@ -478,6 +556,34 @@ class Batch:
     def set_test_hooks(self, grid_barrier_skew: int = 0, timeout_s: float = 0.0):
         _check_batch(lib().apc_batch_set_test_hooks(self.handle, int(grid_barrier_skew), float(timeout_s)),
                      self.handle)
+
+    def forward(self, T: int, B=None, stream=None):
+        """Reset (with new right-hand sides B, one n_s x k tensor per system, or
+        the stored ones), T iterations and every system's xbar(T), in one call
+        (apc_batch_forward)."""
+        import torch
+        arr = None
+        if B is not None:
+            B = [_batch_rhs(b_, n_, self.k) for b_, n_ in zip(B, self.n)]
+            arr = (C.c_void_p * len(B))(*[b_.data_ptr() for b_ in B])
+            self._B = B
+        outs = [torch.empty((n_, self.k), dtype=torch.float64, device=self.device) for n_ in self.n]
+        oarr = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        with _device(self.device):
+            _check_batch(lib().apc_batch_forward(self.handle, arr, int(T), oarr, _stream(stream)), self.handle)
+        return outs
+
+    def backward(self, G, T: int, stream=None):
+        """dL/dB_s for every system from G_s = dL/dxbar_s(T) (n_s x k each)
+        through T iterations (apc_batch_backward)."""
+        import torch
+        G = [_batch_rhs(g_, n_, self.k) for g_, n_ in zip(G, self.n)]
+        garr = (C.c_void_p * len(G))(*[g_.data_ptr() for g_ in G])
+        outs = [torch.empty((n_, self.k), dtype=torch.float64, device=self.device) for n_ in self.n]
+        oarr = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+        with _device(self.device):
+            _check_batch(lib().apc_batch_backward(self.handle, garr, int(T), oarr, _stream(stream)), self.handle)
+        return outs
 
 
 def _device(dev):

@@ -53,8 +53,9 @@ int dalloc(apc_ctx *ctx, T **p, size_t bytes) {
 }
 
 void free_all(apc_ctx *c) {
-    void *ps[] = {c->d_rowstart, c->d_p, c->A, c->b, c->dinv, c->Rinv1, c->Rinv2, c->Q, c->xw, c->xbar,
-                  c->zbuf, c->bar, c->err, c->sums, c->xtmp, c->rtmp, c->xacc, c->rhs, c->d_perm};
+    void *ps[] = {c->d_rowstart, c->d_p, c->A, c->b, c->dinv, c->Rinv1, c->Rinv2, c->R1, c->R2, c->Q, c->xw,
+                  c->xbar, c->zbuf, c->bar, c->err, c->sums, c->xtmp, c->rtmp, c->xacc, c->rhs, c->d_perm,
+                  c->zpart};
     for (void *p : ps)
         if (p) cudaFree(p);
 }
@@ -154,6 +155,8 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         split(1.0 - eta, a.e1_hi, a.e1_lo);
         a.timeout_ns = uint64_t(c->timeout_s * 1e9);
         a.barrier_skew = c->test_barrier_skew;
+        a.zpart = c->zpart;
+        a.det = c->det;
         CK(c, cudaMemsetAsync(c->bar, 0, sizeof(uint32_t), s));
         cudaError_t e = launch_iter(c->precision, c->cpl, a, c->clusters, c->smem, s);
         if (e != cudaSuccess) return fail(c, APC_ERR_LAUNCH, "iteration kernel launch failed: %s", cudaGetErrorString(e));
@@ -169,6 +172,23 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
             return fail(c, APC_ERR_TIMEOUT, "device wait timed out (%s)", what[herr >= 1 && herr <= 3 ? herr : 0]);
         }
     }
+    return APC_OK;
+}
+
+// Free residual monitor of the current xbar: sqrt(sum_b ||D^{-1} R'^T z_b||^2) /
+// ||rhs|| with z the coefficients of the next pass (see launch_monitor) and
+// rhs the right-hand side of the last reset.
+int monitor(apc_ctx *c, double *rel, cudaStream_t s) {
+    if (c->t == 0) return fail(c, APC_ERR_INVALID_ARG, "no forward iteration state (apc_reset first)");
+    const size_t ssz = s_elem_size(c->precision);
+    const void *z = static_cast<const char *>(c->zbuf) + ssz * size_t(c->t % 3) * c->m * c->P;
+    CK(c, cudaMemsetAsync(c->sums + 3, 0, sizeof(double), s));
+    CK(c, launch_monitor(z, state_prec(c->precision), c->d_rowstart, c->d_p, c->dinv, c->R1, c->R2, c->m, c->P,
+                         c->sums + 3, s));
+    double h[2];
+    CK(c, cudaMemcpyAsync(h, c->sums + 2, sizeof(h), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    *rel = h[0] > 0 ? std::sqrt(h[1] / h[0]) : std::sqrt(h[1]);
     return APC_OK;
 }
 
@@ -329,6 +349,8 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     ALLOC(c->dinv, sizeof(double) * N);
     ALLOC(c->Rinv1, sizeof(double) * m * P * P);
     ALLOC(c->Rinv2, sizeof(double) * m * P * P);
+    ALLOC(c->R1, sizeof(double) * m * P * P);
+    ALLOC(c->R2, sizeof(double) * m * P * P);
     ALLOC(c->err, sizeof(int) * 4);
     ALLOC(c->bar, sizeof(uint32_t) * 4);
     ALLOC(c->sums, sizeof(double) * 4);
@@ -402,10 +424,12 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
     CKB2(launch_gram(c->A, n, c->d_rowstart, c->d_p, c->dinv, m, int(P), n, G, s));
     CKB2(launch_chol(G, c->Rinv1, c->d_p, m, int(P), 1e-14, c->err + 2, s));
+    CKB2(cudaMemcpyAsync(c->R1, G, sizeof(double) * m * P * P, cudaMemcpyDeviceToDevice, s));
     CKB2(launch_qt(c->A, n, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, m, int(P), n, QT1, s));
     CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
     CKB2(launch_gram(QT1, n, rs2, c->d_p, nullptr, m, int(P), n, G, s));
     CKB2(launch_chol(G, c->Rinv2, c->d_p, m, int(P), 1e-14, c->err + 3, s));
+    CKB2(cudaMemcpyAsync(c->R2, G, sizeof(double) * m * P * P, cudaMemcpyDeviceToDevice, s));
     CKB2(launch_qt(QT1, n, rs2, c->d_p, nullptr, c->Rinv2, m, int(P), n, QT2, s));
     c->q_bytes = size_t(n) * m * P * q_elem_size(precision);
     if (dalloc(c, &c->Q, c->q_bytes)) return bail2(APC_ERR_NOMEM);
@@ -461,6 +485,8 @@ int reset_blocked(apc_ctx *c, const double *rhs_dev, cudaStream_t s) {
     CK(c, cudaMemsetAsync(c->xbar, 0, sizeof(double) * c->n, s));
     CK(c, launch_csolve(rhs, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->m, c->P,
                         state_prec(c->precision), c->zbuf, s));
+    CK(c, cudaMemsetAsync(c->sums + 2, 0, sizeof(double), s));  // ||rhs||^2 for the monitor
+    CK(c, launch_sumsq(rhs, c->N, c->sums + 2, s));
     c->t = 0;
     return run_pass(c, MODE_INIT, 1.0, 1.0, 1, s);
 }
@@ -514,6 +540,11 @@ int apc_residual(apc_ctx *c, const double *x_dev, const double *rhs_dev, double 
     return APC_OK;
 }
 
+int apc_monitor(apc_ctx *c, double *rel_residual_host, void *stream) {
+    if (!c || !rel_residual_host) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    return monitor(c, rel_residual_host, static_cast<cudaStream_t>(stream));
+}
+
 int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iters, int64_t check_every,
               int32_t refine, double *x_dev, apc_stats *stats, void *stream) {
     if (!c || !x_dev) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
@@ -521,38 +552,65 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
     if (check_every <= 0) check_every = 100;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const auto t_start = std::chrono::steady_clock::now();
-    int64_t iters = 0;
+    int64_t iters = 0, rchecks = 0, mchecks = 0;
     int sweeps = 0;
     double rel = 0.0;
     int rc = APC_OK;
+    // The free monitor (R'^T z, the invariant of App. A) equals the residual to
+    // the precision of the stored bases: FP64 and FP32 contexts use it for the
+    // checks between FP64 residuals; BF16 bases (relative error 2^-9) would put
+    // its error near 4e-3 of ||b||, so BF16 checks stay FP64 residuals.
+    const bool use_monitor = c->precision != APC_BF16;
+    const int kFullEvery = 8;  // an FP64 residual at least every 8 monitor checks
     if (!refine) {
         sweeps = 1;
         if ((rc = reset_blocked(c, nullptr, s)) != APC_OK) return rc;
         CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
         if ((rc = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return rc;
+        ++rchecks;
         const double rel0 = rel;
+        bool exact = true;  // rel is an FP64 residual of the current xbar (copied to x_dev)
+        int since_full = 0;
         rc = APC_ERR_NOT_CONVERGED;
         while (iters < max_iters) {
-            if (rel <= tol) { rc = APC_OK; break; }
+            if (rel <= tol && exact) { rc = APC_OK; break; }
             const int64_t k = std::min(check_every, max_iters - iters);
             int r2 = run_pass(c, MODE_APC, gamma, eta, k, s);
             if (r2 != APC_OK) return r2;
             iters += k;
-            CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
-            if ((r2 = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return r2;
+            bool full = !use_monitor || iters >= max_iters;
+            if (!full) {
+                if ((r2 = monitor(c, &rel, s)) != APC_OK) return r2;
+                ++mchecks;
+                exact = false;
+                full = rel <= tol || !std::isfinite(rel) || ++since_full >= kFullEvery;
+            }
+            if (full) {
+                CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+                if ((r2 = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return r2;
+                ++rchecks;
+                exact = true;
+                since_full = 0;
+            }
             if (!std::isfinite(rel)) { rc = fail(c, APC_ERR_NONFINITE, "iterate became non-finite"); break; }
             if (rel > 1e8 * std::max(rel0, 1e-300)) { rc = fail(c, APC_ERR_DIVERGED, "residual grew to %g", rel); break; }
         }
+        if (!exact) {
+            CK(c, cudaMemcpyAsync(x_dev, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+            if ((rc = residual(c, x_dev, c->b, c->rtmp, &rel, s)) != APC_OK) return rc;
+            ++rchecks;
+        }
         if (rc == APC_OK || rc == APC_ERR_NOT_CONVERGED) {
             if (rel <= tol) rc = APC_OK;
-            else fail(c, APC_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %lld iterations", rel, tol,
-                      (long long)iters);
+            else rc = fail(c, APC_ERR_NOT_CONVERGED, "relative residual %g > tol %g after %lld iterations", rel,
+                           tol, (long long)iters);
         }
     } else {
         // FP64 iterative refinement: x <- x + delta, A delta ~= r = b - A x by APC
         CK(c, cudaMemsetAsync(c->xacc, 0, sizeof(double) * c->n, s));
         CK(c, cudaMemcpyAsync(c->rhs, c->b, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, s));
         if ((rc = residual(c, c->xacc, c->b, c->rhs, &rel, s)) != APC_OK) return rc;
+        ++rchecks;
         rc = APC_ERR_NOT_CONVERGED;
         const int max_sweeps = 64;
         while (iters < max_iters && sweeps < max_sweeps) {
@@ -560,25 +618,32 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
             ++sweeps;
             int r2 = reset_blocked(c, c->rhs, s);
             if (r2 != APC_OK) return r2;
-            double best = 1.0, prev = 1.0, inner = 1.0;
-            // inner APC on A delta = r; stop when its residual stagnates
+            double prev = 1.0, inner = 1.0;
+            // inner APC on A delta = r; stop when its residual (relative to r)
+            // is below 1e-4, stagnates, or suffices for the outer tolerance
             while (iters < max_iters) {
                 const int64_t k = std::min(check_every, max_iters - iters);
                 if ((r2 = run_pass(c, MODE_APC, gamma, eta, k, s)) != APC_OK) return r2;
                 iters += k;
-                CK(c, cudaMemcpyAsync(c->xtmp, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
-                if ((r2 = residual(c, c->xtmp, c->rhs, c->rtmp, &inner, s)) != APC_OK) return r2;
+                if (use_monitor) {
+                    if ((r2 = monitor(c, &inner, s)) != APC_OK) return r2;
+                    ++mchecks;
+                } else {
+                    CK(c, cudaMemcpyAsync(c->xtmp, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
+                    if ((r2 = residual(c, c->xtmp, c->rhs, c->rtmp, &inner, s)) != APC_OK) return r2;
+                    ++rchecks;
+                }
                 if (!std::isfinite(inner)) return fail(c, APC_ERR_NONFINITE, "inner iterate became non-finite");
                 if (inner > 1e8) return fail(c, APC_ERR_DIVERGED, "inner residual grew to %g", inner);
                 const bool stalled = inner > 0.9 * prev && inner < 0.5;
                 prev = inner;
-                best = std::min(best, inner);
                 if (inner <= 1e-4 || stalled || rel * inner <= 0.5 * tol) break;
             }
+            CK(c, cudaMemcpyAsync(c->xtmp, c->xbar, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
             CK(c, launch_axpy_f64(c->xacc, c->xtmp, 1.0, c->n, s));
             if ((r2 = residual(c, c->xacc, c->b, c->rhs, &rel, s)) != APC_OK) return r2;
+            ++rchecks;
             if (!std::isfinite(rel)) return fail(c, APC_ERR_NONFINITE, "refined iterate became non-finite");
-            (void)best;
         }
         CK(c, cudaMemcpyAsync(x_dev, c->xacc, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, s));
         CK(c, cudaStreamSynchronize(s));
@@ -590,6 +655,8 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
         stats->sweeps = sweeps;
         stats->rel_residual = rel;
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+        stats->residual_checks = rchecks;
+        stats->monitor_checks = mchecks;
     }
     return rc;
 }
@@ -731,6 +798,90 @@ int apc_backward_params(apc_ctx *c, const double *g_dev, const double *b_dev, in
     return rc;
 }
 
+int apc_set_deterministic(apc_ctx *c, int32_t on) {
+    if (!c) return fail(nullptr, APC_ERR_INVALID_ARG, "NULL context");
+    if (on && !c->zpart) {
+        const size_t bytes = s_elem_size(c->precision) * size_t(c->clusters) * c->m * c->P;
+        if (cudaMalloc(&c->zpart, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->zpart = nullptr;
+            return fail(c, APC_ERR_NOMEM, "cudaMalloc of %zu bytes (per-cluster partial sums) failed", bytes);
+        }
+    }
+    c->det = on ? 1 : 0;
+    return APC_OK;
+}
+
+namespace {
+// Header of an exported iteration state (apc_export_state).
+struct StateHeader {
+    uint64_t magic;
+    uint32_t version;
+    int32_t precision;
+    int64_t n, N;
+    int32_t m, P;
+    int64_t t;
+    uint64_t payload;
+    double rhs_norm2;  // ||rhs||^2 of the last reset (the monitor's denominator)
+};
+constexpr uint64_t kStateMagic = 0x4554415453435041ull;  // "APCSTATE"
+
+size_t state_payload(const apc_ctx *c) {
+    const size_t ssz = s_elem_size(c->precision);
+    return ssz * size_t(c->n) * c->m + sizeof(double) * size_t(c->n) + ssz * 3 * size_t(c->m) * c->P;
+}
+}  // namespace
+
+int apc_state_bytes(const apc_ctx *c, size_t *bytes) {
+    if (!c || !bytes) return APC_ERR_INVALID_ARG;
+    *bytes = sizeof(StateHeader) + state_payload(c);
+    return APC_OK;
+}
+
+int apc_export_state(apc_ctx *c, void *host_buf, size_t bytes, void *stream) {
+    if (!c || !host_buf) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    const size_t need = sizeof(StateHeader) + state_payload(c);
+    if (bytes < need) return fail(c, APC_ERR_INVALID_ARG, "buffer of %zu bytes; the state needs %zu", bytes, need);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StateHeader h = {kStateMagic, 1u, c->precision, c->n, c->N, c->m, c->P, c->t, state_payload(c), 0.0};
+    CK(c, cudaMemcpyAsync(&h.rhs_norm2, c->sums + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    char *p = static_cast<char *>(host_buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t ssz = s_elem_size(c->precision);
+    const size_t bx = ssz * size_t(c->n) * c->m, bb = sizeof(double) * size_t(c->n), bz = ssz * 3 * size_t(c->m) * c->P;
+    CK(c, cudaMemcpyAsync(p, c->xw, bx, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(p + bx, c->xbar, bb, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaMemcpyAsync(p + bx + bb, c->zbuf, bz, cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    return APC_OK;
+}
+
+int apc_import_state(apc_ctx *c, const void *host_buf, size_t bytes, void *stream) {
+    if (!c || !host_buf) return fail(c, APC_ERR_INVALID_ARG, "NULL argument");
+    StateHeader h;
+    if (bytes < sizeof(h)) return fail(c, APC_ERR_INVALID_ARG, "buffer shorter than the state header");
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1u)
+        return fail(c, APC_ERR_INVALID_ARG, "not an exported APC state (magic or version)");
+    if (h.precision != c->precision || h.n != c->n || h.N != c->N || h.m != c->m || h.P != c->P ||
+        h.payload != state_payload(c))
+        return fail(c, APC_ERR_INVALID_ARG, "the state belongs to another problem shape or precision");
+    if (bytes < sizeof(h) + h.payload) return fail(c, APC_ERR_INVALID_ARG, "buffer shorter than the state");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const char *p = static_cast<const char *>(host_buf) + sizeof(h);
+    const size_t ssz = s_elem_size(c->precision);
+    const size_t bx = ssz * size_t(c->n) * c->m, bb = sizeof(double) * size_t(c->n), bz = ssz * 3 * size_t(c->m) * c->P;
+    CK(c, cudaMemcpyAsync(c->xw, p, bx, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->xbar, p + bx, bb, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->zbuf, p + bx + bb, bz, cudaMemcpyHostToDevice, s));
+    CK(c, cudaMemcpyAsync(c->sums + 2, &h.rhs_norm2, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(c, cudaStreamSynchronize(s));
+    c->t = h.t;
+    return APC_OK;
+}
+
 int apc_set_test_hooks(apc_ctx *c, int32_t grid_barrier_skew, double timeout_s) {
     if (!c || grid_barrier_skew < 0 || !(timeout_s > 0.0)) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
     c->test_barrier_skew = uint32_t(grid_barrier_skew);
@@ -756,6 +907,7 @@ const char *apc_last_error(const apc_ctx *c) { return c ? c->last_error.c_str() 
 
 void apc_destroy(apc_ctx *c) {
     if (!c) return;
+    apc::destroy_multi_rhs(c);
     free_all(c);
     delete c;
 }

@@ -107,11 +107,13 @@ struct SysDesc {
     uint8_t *Zop;            // z planes, B operand of sweep A (see op_offset), Cq x 2kp BF16
     const float *Ct;         // [kp][Cq] c_i, FP32
     const int *coloff;       // [m + 1], multiples of 16
-    float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float
+    float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float; reverse sweep: ell
+    float *Gc;               // [kp][Cq]  reverse sweep: dL/dc_i accumulated (FP32)
     int npad, m, Cq, C;
     int nuA, nuB;            // units of this system in sweep A and in sweep B
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo, im_hi, im_lo;
     float na_hi, na_lo, hb_hi, hb_lo;  // heavy ball: -alpha and beta
+    float omg_hi, omg_lo, gm_hi, gm_lo;  // reverse sweep: 1 - gamma and gamma m
 };
 
 struct BatchArgs {
@@ -124,6 +126,7 @@ struct BatchArgs {
     int64_t iters;
     int init;
     int hb;              // 1: distributed-preconditioned heavy ball instead of APC
+    int adj;             // 1: reverse sweep through `iters` steps (apc_batch_backward)
     uint32_t barrier_skew;  // test hook: added to every cross-CTA wait target (0 = normal)
     uint32_t *bar;          // grid barrier after the initialisation (zero at launch)
     int *err;
@@ -422,9 +425,12 @@ __device__ void store_xop(const SysDesc &d, int64_t row, const float (&xo)[16 * 
 // w_i = the two planes' accumulators summed, then
 // x_i <- x_i + gamma (xbar - x_i - w_i) and the running row sum; at the end
 // the master's row update (double-float) and the xbar' planes of sweep B.
-template <int MT>
+// Reverse sweep (kAdj, one accumulation over every machine, like heavy ball):
+// the step's row update of (ell, lbar) and the planes of the next mu.
+template <int MT, bool kAdj>
 __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
-                                 const SysDesc &d, int row0, bool init, bool hb, float gh, float gl, uint32_t tmem) {
+                                 const SysDesc &d, int row0, bool init, bool hb, float gh, float gl, uint32_t tmem,
+                                 bool last) {
     constexpr int KP = 16 * MT, NA = kPlanesA * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = warp >> 2, quad = warp & 3;
@@ -498,7 +504,33 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
     }
     if (!wact) return;
     float (&xo)[KP] = S;  // the new xbar (hi part), in place of the row sums
-    if (hb) {
+    if constexpr (kAdj) {
+        // one step of the reverse sweep through the affine form of App. A.
+        // Every machine's adjoint is the same vector ell (all start at zero and
+        // follow the same recursion), so per row, with W = sum_i Q_i v_i and
+        // v = Q^T mu from sweep B:
+        //   mu = ell + (eta/m) lbar,  ell' = (1 - gamma) mu,
+        //   lbar' = (1 - eta) lbar + gamma (m mu - W),
+        // and the next mu (ell' + lbar'/m after the last step) to sweep B
+        const float2 em = make_float2(d.em_hi, d.em_lo), e1 = make_float2(d.e1_hi, d.e1_lo);
+        const float2 om = make_float2(d.omg_hi, d.omg_lo), gm = make_float2(d.gm_hi, d.gm_lo);
+        const float2 ng = make_float2(-d.g_hi, -d.g_lo);
+        const float2 nx = last ? make_float2(d.im_hi, d.im_lo) : em;
+        char *xb = reinterpret_cast<char *>(d.Xb + grow), *mb = reinterpret_cast<char *>(d.Mb + grow);
+        const uint32_t ns = opaque_u32(uint32_t(d.npad) * 8u);
+#pragma unroll
+        for (int q = 0; q < KP; ++q) {
+            float2 *lq = reinterpret_cast<float2 *>(mb + size_t(q) * ns);
+            float2 *bq = reinterpret_cast<float2 *>(xb + size_t(q) * ns);
+            const float2 l = __ldcg(lq), lb = __ldcg(bq);
+            const float2 mu = dfa(l, dfm(em, lb));
+            const float2 ln = dfm(om, mu);
+            const float2 lbn = dfa(dfa(dfm(e1, lb), dfm(gm, mu)), dfm(ng, make_float2(W[q], 0.0f)));
+            __stcg(lq, ln);
+            __stcg(bq, lbn);
+            xo[q] = dfa(ln, dfm(nx, lbn)).x;
+        }
+    } else if (hb) {
         // heavy ball on the preconditioned system (Sec. 4.3 update, Sec. 6):
         // W holds the gradient sum_i Q_i (Q_i^T x - c_i);
         // zeta <- beta zeta + gradient, x <- x - alpha zeta
@@ -573,6 +605,34 @@ __device__ void store_z(const SysDesc &d, int col, const float (&Y)[16 * MT], bo
     }
 }
 
+// Reverse sweep: v = Y of column `col` (Y = Q^T mu) added to dL/dc with
+// weight gamma (1 at the end of the sweep, the initialisation's term) and, except
+// at the end, split into two BF16 planes for sweep A (the layout of store_z).
+template <int MT>
+__device__ void store_v(const SysDesc &d, int col, const float (&Y)[16 * MT], bool fin) {
+    constexpr int KP = 16 * MT, NA = kPlanesA * KP;
+    const int lane = threadIdx.x & 31;
+    char *gc = reinterpret_cast<char *>(d.Gc + col);
+    const uint32_t cs = opaque_u32(uint32_t(d.Cq) * 4u);
+    const float gh = fin ? 1.0f : d.g_hi, gl = fin ? 0.0f : d.g_lo;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        float *gq = reinterpret_cast<float *>(gc + size_t(q) * cs);
+        const float y = Y[q];
+        __stcg(gq, __ldcg(gq) + fmaf(gh, y, gl * y));
+        if (!fin) {
+            const float y1 = __shfl_down_sync(0xffffffffu, y, 1);
+            if ((lane & 1) == 0) {
+                uint32_t w[kPlanesA];
+                split2<kPlanesA>(y, y1, w);
+#pragma unroll
+                for (int p = 0; p < kPlanesA; ++p)
+                    __stcg(reinterpret_cast<uint32_t *>(d.Zop + op_offset(NA, p * KP + q, col)), w[p]);
+            }
+        }
+    }
+}
+
 // Tensor-core warp, sweep B: D_h += Q[rows, 128 columns]^T Xop[rows, planes x
 // rhs] for the unit's M-tiles h (A: the stage's 64-column blocks read
 // MN-major, 128-byte swizzle, 4 KB between blocks; B: the xbar' planes, core
@@ -608,10 +668,11 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
 
 // Consumers, sweep B: thread = one column (warp w: M-tiles w/4 and w/4 + 2,
 // columns 32 (w%4) .. + 31 of each, the tensor-memory lanes of its quarter):
-// Y = the three planes' accumulators summed, then z = Y - c to sweep A.
-template <int MT>
+// Y = the three planes' accumulators summed, then z = Y - c to sweep A
+// (reverse sweep: v = Y, see store_v).
+template <int MT, bool kAdj>
 __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree, const SysDesc &d,
-                                 int col0, uint32_t tmem) {
+                                 int col0, uint32_t tmem, bool fin) {
     constexpr int KP = 16 * MT, NB = kPlanesB * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3;
     const int ncols = min(kColsB, d.Cq - col0);
@@ -645,7 +706,10 @@ __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, 
     for (int hh = 0; hh < 2; ++hh) {
         const int h = (warp >> 2) + 2 * hh;
         const int cl = 128 * h + 32 * quad;
-        if (cl < ncols) store_z<MT>(d, col0 + cl + lane, Y[hh], false);
+        if (cl < ncols) {
+            if constexpr (kAdj) store_v<MT>(d, col0 + cl + lane, Y[hh], fin);
+            else store_z<MT>(d, col0 + cl + lane, Y[hh], false);
+        }
     }
 }
 
@@ -685,7 +749,7 @@ __device__ bool wait_count(const unsigned long long *p, unsigned long long targe
     return false;
 }
 
-template <int MT>
+template <int MT, bool kAdj>
 __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ int abort_flag;
@@ -757,20 +821,34 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     // dependency lies earlier in the stream and every CTA takes its units in
     // stream order, so the earliest incomplete unit can always proceed.  A
     // claim past the end hands over -1 and ends the stream.
-    const long long per_it = (long long)a.nA + a.nB, total = (long long)a.iters * per_it;
+    // Reverse sweep (kAdj): step it is its sweep-B units (v = Q^T mu), then its
+    // sweep-A units (sum_i Q_i v_i and the row update); `iters` steps and a
+    // last sweep B for the initialisation's term.  Sweep B of step it needs
+    // sweep A of it - 1 (mu), sweep A of it needs sweep B of it (v).
+    const long long per_it = (long long)a.nA + a.nB;
+    const long long total = kAdj ? ((long long)a.iters + 1) * per_it - a.nA : (long long)a.iters * per_it;
     struct Unit {
         long long it;
-        bool is_a, init, hb;
+        bool is_a, init, hb, edge;  // edge: last step's sweep A / final sweep B of a reverse sweep
         int2 U;
     };
     auto decode = [&](long long g) {
         Unit u;
         u.it = g / per_it;
         const int r = int(g - u.it * per_it);
-        u.is_a = r < a.nA;
-        u.U = u.is_a ? a.unitsA[r] : a.unitsB[r - a.nA];
-        u.init = a.init && u.it == 0;
-        u.hb = a.hb && !u.init;
+        if constexpr (kAdj) {
+            u.is_a = r >= a.nB;
+            u.U = u.is_a ? a.unitsA[r - a.nB] : a.unitsB[r];
+            u.init = false;
+            u.hb = true;
+            u.edge = u.is_a ? u.it + 1 == a.iters : u.it == a.iters;
+        } else {
+            u.is_a = r < a.nA;
+            u.U = u.is_a ? a.unitsA[r] : a.unitsB[r - a.nA];
+            u.init = a.init && u.it == 0;
+            u.hb = a.hb && !u.init;
+            u.edge = false;
+        }
         return u;
     };
     auto run = [&]() {
@@ -792,9 +870,14 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                     const unsigned long long nb = (unsigned long long)kConsumerWarps * unsigned(d.nuB);
                     const unsigned long long it = (unsigned long long)u.it, sk = a.barrier_skew;
                     const unsigned long long *dn = a.done + 2 * u.U.x;
-                    const bool ready = u.is_a ? wait_count(dn, it * na + sk, a, &abort_flag) &&
-                                                    wait_count(dn + 1, it * nb + sk, a, &abort_flag)
-                                              : wait_count(dn, (it + 1) * na + sk, a, &abort_flag);
+                    bool ready;
+                    if constexpr (kAdj)
+                        ready = u.is_a ? wait_count(dn + 1, (it + 1) * nb + sk, a, &abort_flag)
+                                       : wait_count(dn, it * na + sk, a, &abort_flag);
+                    else
+                        ready = u.is_a ? wait_count(dn, it * na + sk, a, &abort_flag) &&
+                                             wait_count(dn + 1, it * nb + sk, a, &abort_flag)
+                                       : wait_count(dn, (it + 1) * na + sk, a, &abort_flag);
                     if (ready) __threadfence();
                     else g = -1;
                 }
@@ -845,10 +928,10 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 const Unit u = decode(g);
                 const SysDesc &d = a.sys[u.U.x];
                 if (u.is_a)
-                    sweep_a_consumer<MT>(R, cur, mc, dfull, dfree, d, u.U.y, u.init, u.hb, u.init ? 1.0f : d.g_hi,
-                                         u.init ? 0.0f : d.g_lo, tmem);
+                    sweep_a_consumer<MT, kAdj>(R, cur, mc, dfull, dfree, d, u.U.y, u.init, u.hb,
+                                               u.init ? 1.0f : d.g_hi, u.init ? 0.0f : d.g_lo, tmem, u.edge);
                 else
-                    sweep_b_consumer<MT>(R, ubc, bfull, bfree, d, u.U.y, tmem);
+                    sweep_b_consumer<MT, kAdj>(R, ubc, bfull, bfree, d, u.U.y, tmem, u.edge);
                 __syncwarp();
                 if (*reinterpret_cast<volatile int *>(&abort_flag)) return;
                 // the unit's global writes are read by other CTAs (bulk
@@ -861,7 +944,7 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
         }
     };
 
-    if (a.init) {
+    if (!kAdj && a.init) {
         // z_i(0) = -c_i, so that sweep A with gamma = 1 and x = xbar = 0 forms
         // the least-norm x_i(0) = Q_i c_i (Algorithm 1) and xbar(0) their mean
         if (consumer)
@@ -972,6 +1055,56 @@ __global__ void x_out_kernel(const float *X, int64_t n, int npad, int m, int kp,
     }
 }
 
+// Start of the reverse sweep for one system: lbar = g (double-float), ell = 0,
+// and the three BF16 planes of mu = coef * g (the B operand of sweep B, layout
+// of store_xop), zero on padded rows and right-hand sides.  G is n x k, ld k.
+__global__ void adj_seed_kernel(const double *G, int64_t n, int k, int kp, int npad, double coef, float2 *Xb,
+                                float2 *Mb, uint8_t *Xop) {
+    const int NB = kPlanesB * kp;
+    const int64_t total = int64_t(npad) * kp;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int q = int(i / npad);
+        const int64_t j = i - int64_t(q) * npad;
+        const double gv = (j < n && q < k) ? G[j * k + q] : 0.0;
+        const float hi = float(gv);
+        Xb[size_t(q) * npad + j] = make_float2(hi, float(gv - double(hi)));
+        Mb[size_t(q) * npad + j] = make_float2(0.0f, 0.0f);
+        float x = float(coef * gv);
+        for (int p = 0; p < kPlanesB; ++p) {
+            const __nv_bfloat16 v = __float2bfloat16_rn(x);
+            x -= __bfloat162float(v);
+            *reinterpret_cast<__nv_bfloat16 *>(Xop + op_offset(NB, p * kp + q, j)) = v;
+        }
+    }
+}
+
+// End of the reverse sweep: dL/db_b = d .* (R1inv_b (R2inv_b dL/dc_b)) (the
+// transpose of c_b = R2inv_b^T R1inv_b^T (d .* b_b), batch_coef_kernel), one
+// block and right-hand side per CTA, FP64; DB is n x k, ld k.
+__global__ void batch_grad_kernel(const float *Gc, int Cq, const int *coloff, const int64_t *row_start,
+                                  const int32_t *pcount, const double *dinv, const double *Rinv1,
+                                  const double *Rinv2, int P, int k, double *DB) {
+    extern __shared__ double sh[];  // g[P], w[P]
+    const int b = blockIdx.x, rhs = blockIdx.y;
+    const int p = pcount[b];
+    const int64_t r0 = row_start[b];
+    const double *R1 = Rinv1 + size_t(b) * P * P, *R2 = Rinv2 + size_t(b) * P * P;
+    double *g = sh, *w = sh + P;
+    for (int c = threadIdx.x; c < P; c += blockDim.x) g[c] = c < p ? double(Gc[size_t(rhs) * Cq + coloff[b] + c]) : 0.0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < p; r += blockDim.x) {
+        double acc = 0.0;
+        for (int c = r; c < p; ++c) acc = fma(R2[size_t(r) * P + c], g[c], acc);
+        w[r] = acc;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < p; r += blockDim.x) {
+        double acc = 0.0;
+        for (int c = r; c < p; ++c) acc = fma(R1[size_t(r) * P + c], w[c], acc);
+        DB[(r0 + r) * k + rhs] = dinv[r0 + r] * acc;
+    }
+}
+
 void split_f64(double v, float &hi, float &lo) {
     hi = float(v);
     lo = float(v - double(hi));
@@ -999,9 +1132,12 @@ struct apc_batch {
     int64_t q_bytes = 0, state_bytes = 0;
     double timeout_s = 2.0;
     uint32_t barrier_skew = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;  // forward launch (APC or heavy ball)
     int64_t graph_iters = -1;
-    int graph_method = -1;
+    int graph_method = -1;            // method of the captured forward launch
+    cudaGraphExec_t graph_adj = nullptr;  // reverse sweep (apc_batch_backward)
+    int64_t graph_adj_iters = -1;
+    std::vector<double> eta;  // eta_s of apc_batch_set_params (the reverse sweep's seed)
     std::string last_error;
 };
 
@@ -1035,9 +1171,12 @@ int balloc(apc_batch *b, T **p, size_t bytes) {
     return APC_OK;
 }
 
-const void *kernel_ptr(int MT) {
-    return MT == 1 ? reinterpret_cast<const void *>(&apc_batch_kernel<1>)
-                   : reinterpret_cast<const void *>(&apc_batch_kernel<2>);
+const void *kernel_ptr(int MT, bool adj) {
+    if (adj)
+        return MT == 1 ? reinterpret_cast<const void *>(&apc_batch_kernel<1, true>)
+                       : reinterpret_cast<const void *>(&apc_batch_kernel<2, true>);
+    return MT == 1 ? reinterpret_cast<const void *>(&apc_batch_kernel<1, false>)
+                   : reinterpret_cast<const void *>(&apc_batch_kernel<2, false>);
 }
 
 // Units sorted by decreasing key, equal keys in insertion order; the CTAs
@@ -1051,7 +1190,7 @@ std::vector<int2> by_key_desc(std::vector<std::pair<double, int2>> items) {
     return units;
 }
 
-int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
+int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s, bool adj = false) {
     BatchArgs a = {};
     a.sys = b->d_desc;
     a.unitsA = b->d_unitsA;
@@ -1062,16 +1201,24 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s) {
     a.done = b->ctr + 2;
     a.iters = iters;
     a.init = init;
-    a.hb = init ? 0 : b->method;
+    a.hb = init || adj ? 0 : b->method;
+    a.adj = adj ? 1 : 0;
     a.barrier_skew = b->barrier_skew;
     a.bar = reinterpret_cast<uint32_t *>(b->ctr);
     a.err = b->err;
     a.timeout_ns = uint64_t(b->timeout_s * 1e9);
     BCK(b, cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long) * (2 + 2 * size_t(b->nsys)), s));
-    if (b->MT == 1)
-        apc_batch_kernel<1><<<b->grid, kThreads, kSmemBytes, s>>>(a);
-    else
-        apc_batch_kernel<2><<<b->grid, kThreads, kSmemBytes, s>>>(a);
+    if (adj) {
+        if (b->MT == 1)
+            apc_batch_kernel<1, true><<<b->grid, kThreads, kSmemBytes, s>>>(a);
+        else
+            apc_batch_kernel<2, true><<<b->grid, kThreads, kSmemBytes, s>>>(a);
+    } else {
+        if (b->MT == 1)
+            apc_batch_kernel<1, false><<<b->grid, kThreads, kSmemBytes, s>>>(a);
+        else
+            apc_batch_kernel<2, false><<<b->grid, kThreads, kSmemBytes, s>>>(a);
+    }
     BCK(b, cudaGetLastError());
     return APC_OK;
 }
@@ -1086,6 +1233,42 @@ int check_err(apc_batch *b, cudaStream_t s) {
         return bfail(b, APC_ERR_TIMEOUT, "a wait on another CTA's work ran out of time (%.3g s)", b->timeout_s);
     }
     return APC_OK;
+}
+
+// One persistent launch (counter reset + kernel) of `iters` iterations, or of
+// a reverse sweep through `iters` steps, captured once per (count, method)
+// and replayed as a CUDA graph; then the device error flag is read.
+int run_graph(apc_batch *b, int64_t iters, bool adj, cudaStream_t s) {
+    cudaGraphExec_t &exec = adj ? b->graph_adj : b->graph;
+    const bool stale = adj ? b->graph_adj_iters != iters : (b->graph_iters != iters || b->graph_method != b->method);
+    if (!exec || stale) {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        cudaStream_t cs;
+        BCK(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        const int rc = e == cudaSuccess ? launch(b, 0, iters, cs, adj) : APC_ERR_CUDA;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (rc == APC_OK && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess || rc != APC_OK || e2 != cudaSuccess) {
+            cudaGetLastError();
+            exec = nullptr;
+            return bfail(b, APC_ERR_CUDA, "graph capture of the batched launch failed");
+        }
+        if (adj) {
+            b->graph_adj_iters = iters;
+        } else {
+            b->graph_iters = iters;
+            b->graph_method = b->method;
+        }
+    }
+    BCK(b, cudaGraphLaunch(exec, s));
+    return check_err(b, s);
 }
 
 int compute_coefficients(apc_batch *b, int sys, cudaStream_t s) {
@@ -1250,10 +1433,16 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
     // one CTA per SM, all resident at once (the CTAs wait on one another's units)
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    if (cudaFuncSetAttribute(kernel_ptr(MT), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
+    int per_sm_adj = 0;
+    if (cudaFuncSetAttribute(kernel_ptr(MT, false), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
             cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr(MT), kThreads, kSmemBytes) != cudaSuccess ||
-        per_sm < 1) {
+        cudaFuncSetAttribute(kernel_ptr(MT, true), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr(MT, false), kThreads, kSmemBytes) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_adj, kernel_ptr(MT, true), kThreads, kSmemBytes) !=
+            cudaSuccess ||
+        per_sm < 1 || per_sm_adj < 1) {
         cudaGetLastError();
         bfail(b, APC_ERR_LAUNCH, "the batched kernel cannot be resident (%zu bytes of shared memory)", kSmemBytes);
         return bail(APC_ERR_LAUNCH);
@@ -1300,8 +1489,11 @@ int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *e
         split_f64(g, d.g_hi, d.g_lo);
         split_f64(e / b->m[sys], d.em_hi, d.em_lo);
         split_f64(1.0 - e, d.e1_hi, d.e1_lo);
+        split_f64(1.0 - g, d.omg_hi, d.omg_lo);
+        split_f64(g * b->m[sys], d.gm_hi, d.gm_lo);
     }
     BCK(b, cudaMemcpy(b->d_desc, b->desc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice));
+    b->eta.assign(eta_host, eta_host + b->nsys);
     b->params_set = true;
     b->method = 0;
     return APC_OK;
@@ -1354,33 +1546,62 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     if (iters == 0) return APC_OK;
     if (!b->params_set) return bfail(b, APC_ERR_PARAMS, "apc_batch_set_params must precede apc_batch_iterate");
     if (!b->reset_done) return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_reset must precede apc_batch_iterate");
+    return run_graph(b, iters, false, static_cast<cudaStream_t>(stream));
+}
+
+int apc_batch_forward(apc_batch *b, const double *const *B_dev_host, int64_t T, double *const *X_dev_host,
+                      void *stream) {
+    if (!b || !X_dev_host || T < 0) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
+    for (int sys = 0; sys < b->nsys; ++sys)
+        if (!X_dev_host[sys]) return bfail(b, APC_ERR_INVALID_ARG, "system %d: NULL output", sys);
+    if (!b->params_set || b->method != 0)
+        return bfail(b, APC_ERR_PARAMS, "apc_batch_set_params must precede apc_batch_forward");
+    int rc = apc_batch_reset(b, B_dev_host, stream);
+    if (rc == APC_OK) rc = apc_batch_iterate(b, T, stream);
+    for (int sys = 0; rc == APC_OK && sys < b->nsys; ++sys) rc = apc_batch_get_xbar(b, sys, X_dev_host[sys], b->k, stream);
+    return rc;
+}
+
+int apc_batch_backward(apc_batch *b, const double *const *G_dev_host, int64_t T, double *const *DB_dev_host,
+                       void *stream) {
+    if (!b || !G_dev_host || !DB_dev_host || T < 0) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
+    for (int sys = 0; sys < b->nsys; ++sys)
+        if (!G_dev_host[sys] || !DB_dev_host[sys])
+            return bfail(b, APC_ERR_INVALID_ARG, "system %d: NULL gradient or output", sys);
+    if (!b->params_set || b->method != 0)
+        return bfail(b, APC_ERR_PARAMS, "the reverse sweep needs APC parameters (apc_batch_set_params)");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // one persistent launch (counter reset + kernel), captured once per
-    // iteration count and replayed as a CUDA graph
-    if (!b->graph || b->graph_iters != iters || b->graph_method != b->method) {
-        if (b->graph) {
-            cudaGraphExecDestroy(b->graph);
-            b->graph = nullptr;
+    // dL/dc_i accumulators, allocated on first use
+    if (!b->desc[0].Gc) {
+        for (int sys = 0; sys < b->nsys; ++sys) {
+            int rc = balloc(b, &b->desc[sys].Gc, sizeof(float) * size_t(b->kp) * b->desc[sys].Cq);
+            if (rc != APC_OK) return rc;
         }
-        cudaStream_t cs;
-        BCK(b, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        const cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        const int rc = e == cudaSuccess ? launch(b, 0, iters, cs) : APC_ERR_CUDA;
-        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-        if (rc == APC_OK && e2 == cudaSuccess) e2 = cudaGraphInstantiate(&b->graph, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        if (e != cudaSuccess || rc != APC_OK || e2 != cudaSuccess) {
-            cudaGetLastError();
-            b->graph = nullptr;
-            return bfail(b, APC_ERR_CUDA, "graph capture of the batched launch failed");
-        }
-        b->graph_iters = iters;
-        b->graph_method = b->method;
+        BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, s));
     }
-    BCK(b, cudaGraphLaunch(b->graph, s));
-    return check_err(b, s);
+    // lbar = g, ell = 0, dL/dc = 0, and the planes of mu = ell + (eta/m) lbar
+    // (lbar/m for T = 0: the initialisation's term alone)
+    for (int sys = 0; sys < b->nsys; ++sys) {
+        const SysDesc &d = b->desc[sys];
+        BCK(b, cudaMemsetAsync(d.Gc, 0, sizeof(float) * size_t(b->kp) * d.Cq, s));
+        const double coef = (T == 0 ? 1.0 : b->eta[sys]) / b->m[sys];
+        const unsigned grid = unsigned(std::min<int64_t>((int64_t(d.npad) * b->kp + 255) / 256, 152 * 16));
+        adj_seed_kernel<<<grid, 256, 0, s>>>(G_dev_host[sys], b->n[sys], b->k, b->kp, d.npad, coef, d.Xb, d.Mb,
+                                             d.Xop);
+        BCK(b, cudaGetLastError());
+    }
+    b->reset_done = false;  // the iteration state now holds the reverse sweep
+    int rc = run_graph(b, T, true, s);
+    if (rc != APC_OK) return rc;
+    for (int sys = 0; sys < b->nsys; ++sys) {
+        apc_ctx *c = b->ctx[sys];
+        const SysDesc &d = b->desc[sys];
+        const size_t sh = sizeof(double) * 2 * c->P;
+        batch_grad_kernel<<<dim3(unsigned(c->m), unsigned(b->k)), 128, sh, s>>>(
+            d.Gc, d.Cq, d.coloff, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, c->Rinv2, c->P, b->k, DB_dev_host[sys]);
+        BCK(b, cudaGetLastError());
+    }
+    return APC_OK;
 }
 
 int apc_batch_get_xbar(apc_batch *b, int32_t sys, double *X_dev, int64_t ldx, void *stream) {
@@ -1405,10 +1626,11 @@ int apc_batch_set_test_hooks(apc_batch *b, int32_t grid_barrier_skew, double tim
     if (!b || grid_barrier_skew < 0 || !(timeout_s >= 0.0)) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
     b->barrier_skew = uint32_t(grid_barrier_skew);
     b->timeout_s = timeout_s > 0 ? timeout_s : 2.0;
-    if (b->graph) {
-        cudaGraphExecDestroy(b->graph);
-        b->graph = nullptr;
-    }
+    for (cudaGraphExec_t *g : {&b->graph, &b->graph_adj})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
     return APC_OK;
 }
 
@@ -1425,11 +1647,152 @@ int apc_batch_info(const apc_batch *b, int32_t *nsys, int32_t *k, int64_t *q_byt
     return APC_OK;
 }
 
+}  // extern "C"
+
+// ---- k right-hand sides through a single-system context ------------------------
+
+namespace {
+
+int cfail(apc_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+    apc::set_global_error_text(buf);
+    return code;
+}
+
+#define CCK(c, call)                                                                                     \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return cfail((c), APC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// The tensor-core form applies to a BF16 context of a square system with
+// contiguous blocks and 2..32 right-hand sides; other contexts take the
+// columns one after another through the single-system kernel.
+bool use_tensor_cores(const apc_ctx *c, int64_t k) {
+    return c->precision == APC_BF16 && c->N == c->n && !c->d_perm && k >= 2 && k <= 32;
+}
+
+// The context's one-system batch for k right-hand sides (built on first use,
+// rebuilt when k changes) with (gamma, eta) set.
+int multi_rhs_batch(apc_ctx *c, int64_t k, double gamma, double eta, cudaStream_t s) {
+    if (!c->mrhs || c->mrhs_k != k) {
+        apc::destroy_multi_rhs(c);
+        if (cudaMalloc(&c->mrhs_in, sizeof(double) * c->n * k) != cudaSuccess ||
+            cudaMalloc(&c->mrhs_out, sizeof(double) * c->N * k) != cudaSuccess) {
+            cudaGetLastError();
+            apc::destroy_multi_rhs(c);
+            return cfail(c, APC_ERR_NOMEM, "staging buffers for %lld right-hand sides", (long long)k);
+        }
+        CCK(c, cudaMemsetAsync(c->mrhs_in, 0, sizeof(double) * c->n * k, s));
+        const int64_t n = c->n;
+        const int32_t m = c->m;
+        const double *A = c->A;
+        const double *B = c->mrhs_in;
+        apc_options o = {APC_BF16, 0, 0, c->timeout_s, 0};
+        const int rc = apc_batch_setup(&c->mrhs, 1, &n, &m, c->offs.data(), &A, &B, int32_t(k), &o, s);
+        if (rc != APC_OK) {
+            c->mrhs = nullptr;
+            apc::destroy_multi_rhs(c);
+            return cfail(c, rc, "%s", apc_batch_last_error(nullptr));
+        }
+        c->mrhs_k = int(k);
+    }
+    const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);
+    if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));
+    return APC_OK;
+}
+
+}  // namespace
+
+namespace apc {
+void destroy_multi_rhs(apc_ctx *c) {
+    if (c->mrhs) apc_batch_destroy(c->mrhs);
+    if (c->mrhs_in) cudaFree(c->mrhs_in);
+    if (c->mrhs_out) cudaFree(c->mrhs_out);
+    c->mrhs = nullptr;
+    c->mrhs_in = c->mrhs_out = nullptr;
+    c->mrhs_k = 0;
+}
+}  // namespace apc
+
+extern "C" {
+
+int apc_forward_rhs(apc_ctx *c, const double *B_dev, int64_t k, int64_t ldb, int64_t T, double gamma, double eta,
+                    double *X_dev, int64_t ldx, void *stream) {
+    if (!c) return apc::set_global_error_text("NULL context"), APC_ERR_INVALID_ARG;
+    if (!B_dev || !X_dev || k < 1 || ldb < k || ldx < k || T < 0)
+        return cfail(c, APC_ERR_INVALID_ARG, "apc_forward_rhs: bad pointer, k, leading dimension or T");
+    if (!(gamma > 0.0 && gamma < 2.0) || !std::isfinite(eta))
+        return cfail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2) and eta must be finite", gamma);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (use_tensor_cores(c, k)) {
+        int rc = multi_rhs_batch(c, k, gamma, eta, s);
+        if (rc != APC_OK) return rc;
+        CCK(c, cudaMemcpy2DAsync(c->mrhs_in, sizeof(double) * k, B_dev, sizeof(double) * ldb, sizeof(double) * k,
+                                 c->N, cudaMemcpyDeviceToDevice, s));
+        const double *Bp = c->mrhs_in;
+        double *Xp = c->mrhs_out;
+        rc = apc_batch_forward(c->mrhs, &Bp, T, &Xp, stream);
+        if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));
+        CCK(c, cudaMemcpy2DAsync(X_dev, sizeof(double) * ldx, c->mrhs_out, sizeof(double) * k, sizeof(double) * k,
+                                 c->n, cudaMemcpyDeviceToDevice, s));
+        return APC_OK;
+    }
+    for (int64_t j = 0; j < k; ++j) {
+        CCK(c, cudaMemcpy2DAsync(c->rhs, sizeof(double), B_dev + j, sizeof(double) * ldb, sizeof(double), c->N,
+                                 cudaMemcpyDeviceToDevice, s));
+        int rc = apc_reset(c, c->rhs, stream);
+        if (rc == APC_OK && T > 0) rc = apc_iterate(c, gamma, eta, T, stream);
+        if (rc != APC_OK) return rc;
+        CCK(c, cudaMemcpy2DAsync(X_dev + j, sizeof(double) * ldx, c->xbar, sizeof(double), sizeof(double), c->n,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    return APC_OK;
+}
+
+int apc_backward_rhs(apc_ctx *c, const double *G_dev, int64_t k, int64_t ldg, int64_t T, double gamma, double eta,
+                     double *DB_dev, int64_t lddb, void *stream) {
+    if (!c) return apc::set_global_error_text("NULL context"), APC_ERR_INVALID_ARG;
+    if (!G_dev || !DB_dev || k < 1 || ldg < k || lddb < k || T < 0)
+        return cfail(c, APC_ERR_INVALID_ARG, "apc_backward_rhs: bad pointer, k, leading dimension or T");
+    if (!(gamma > 0.0 && gamma < 2.0) || !std::isfinite(eta))
+        return cfail(c, APC_ERR_PARAMS, "gamma=%g must lie in (0, 2) and eta must be finite", gamma);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (use_tensor_cores(c, k)) {
+        int rc = multi_rhs_batch(c, k, gamma, eta, s);
+        if (rc != APC_OK) return rc;
+        CCK(c, cudaMemcpy2DAsync(c->mrhs_in, sizeof(double) * k, G_dev, sizeof(double) * ldg, sizeof(double) * k,
+                                 c->n, cudaMemcpyDeviceToDevice, s));
+        const double *Gp = c->mrhs_in;
+        double *Dp = c->mrhs_out;
+        rc = apc_batch_backward(c->mrhs, &Gp, T, &Dp, stream);
+        if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));
+        CCK(c, cudaMemcpy2DAsync(DB_dev, sizeof(double) * lddb, c->mrhs_out, sizeof(double) * k, sizeof(double) * k,
+                                 c->N, cudaMemcpyDeviceToDevice, s));
+        return APC_OK;
+    }
+    for (int64_t j = 0; j < k; ++j) {
+        CCK(c, cudaMemcpy2DAsync(c->xtmp, sizeof(double), G_dev + j, sizeof(double) * ldg, sizeof(double), c->n,
+                                 cudaMemcpyDeviceToDevice, s));
+        const int rc = apc_backward(c, c->xtmp, T, gamma, eta, c->rhs, stream);
+        if (rc != APC_OK) return rc;
+        CCK(c, cudaMemcpy2DAsync(DB_dev + j, sizeof(double) * lddb, c->rhs, sizeof(double), sizeof(double), c->N,
+                                 cudaMemcpyDeviceToDevice, s));
+    }
+    return APC_OK;
+}
+
 const char *apc_batch_last_error(const apc_batch *b) { return b ? b->last_error.c_str() : apc_last_error(nullptr); }
 
 void apc_batch_destroy(apc_batch *b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_adj) cudaGraphExecDestroy(b->graph_adj);
     for (void *p : b->owned) cudaFree(p);
     for (apc_ctx *c : b->ctx) apc_destroy(c);
     delete b;

@@ -15,6 +15,7 @@ struct apc_ctx {
     int32_t *d_p = nullptr;          // rows per block
     double *A = nullptr, *b = nullptr, *dinv = nullptr;
     double *Rinv1 = nullptr, *Rinv2 = nullptr;
+    double *R1 = nullptr, *R2 = nullptr;  // the two Cholesky factors (free residual monitor)
     void *Q = nullptr;
     void *xw = nullptr, *zbuf = nullptr;
     double *xbar = nullptr;  // master estimate, FP64 in every mode
@@ -28,11 +29,20 @@ struct apc_ctx {
     double timeout_s = 2.0;
     uint32_t test_barrier_skew = 0;
     size_t q_bytes = 0;
+    void *zpart = nullptr;      // deterministic reduction: per-cluster partial z' [clusters][m][P]
+    int det = 0;
     int64_t *d_perm = nullptr;  // apc_setup_rows: row k of the blocked system is row d_perm[k] of the caller's
+    // k right-hand sides at once (apc_forward_rhs / apc_backward_rhs on a BF16
+    // square context): a one-system batch on the tensor cores, built on first use
+    struct apc_batch *mrhs = nullptr;
+    int mrhs_k = 0;
+    double *mrhs_in = nullptr, *mrhs_out = nullptr;  // n x k staging, leading dimension k
     std::string last_error;
 };
 
 namespace apc {
+// Frees what apc_forward_rhs / apc_backward_rhs built (apc_batch.cu).
+void destroy_multi_rhs(apc_ctx *c);
 // Device element sizes of Q and of the iteration state for a precision.
 inline size_t q_elem_bytes(int precision) { return precision == 0 ? 8 : (precision == 1 ? 4 : 2); }
 inline size_t s_elem_bytes(int precision) { return precision == 0 ? 8 : 4; }

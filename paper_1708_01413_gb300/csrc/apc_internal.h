@@ -39,6 +39,11 @@ struct IterArgs {
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo;
     uint64_t timeout_ns;
     uint32_t barrier_skew;  // test hook: extra arrivals the grid barrier waits for (0 in use)
+    // Deterministic reduction (det != 0): each cluster stores its partial z'
+    // into zpart[cluster][m][P] (TS) and, after a grid barrier, the partials
+    // are summed in cluster order into the z buffer, in place of atomics.
+    void *zpart;
+    int32_t det;
 };
 
 // Device error word values.
@@ -91,6 +96,13 @@ cudaError_t launch_csolve(const double *rhs, const int64_t *row_start_dev, const
 cudaError_t launch_bsolve(const void *z, const int64_t *row_start_dev, const int32_t *p_dev,
                           const double *dinv, const double *Rinv1, const double *Rinv2, int m, int P,
                           int precision, double *db, cudaStream_t s);
+// sums[0] += sum_b ||D_b^{-1} R1_b^T R2_b^T z_b||^2 (z: TS [m][P], the state's
+// precision: 0 = FP64, 1 = FP32; R1, R2 the Cholesky factors [m][P][P]).
+cudaError_t launch_monitor(const void *z, int precision, const int64_t *row_start_dev, const int32_t *p_dev,
+                           const double *dinv, const double *R1, const double *R2, int m, int P, double *sums,
+                           cudaStream_t s);
+// sums[0] += ||v||^2 (FP64).
+cudaError_t launch_sumsq(const double *v, int64_t count, double *sums, cudaStream_t s);
 // out = rhs - A x (FP64); sums[0] += ||out||^2, sums[1] += ||rhs||^2.
 cudaError_t launch_residual(const double *A, int64_t lda, int64_t N, int64_t n, const double *x,
                             const double *rhs, double *out, double *sums, cudaStream_t s);

@@ -623,6 +623,31 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         return false;
     };
 
+    // Bounded grid-wide barrier (the n-th of this launch waits for n * grid
+    // arrivals); true when the wait ran out of time.
+    uint32_t nbar = 0;
+    auto grid_sync = [&]() -> bool {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            red_release_add_u32(a.bar, 1u);
+            const uint32_t target = (nbar + 1) * gridDim.x + a.barrier_skew;
+            if (ld_acquire_u32(a.bar) < target) {
+                const uint64_t t_start = globaltimer_ns();
+                while (ld_acquire_u32(a.bar) < target) {
+                    if (globaltimer_ns() - t_start > a.timeout_ns) {
+                        abort_flag = 1;
+                        abort_code = DEV_TIMEOUT_GRID;
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        ++nbar;
+        return __syncthreads_or(abort_flag);
+    };
+
     for (int64_t it = 0; it < a.iters; ++it) {
         cx_cur = cx0;
         for (int t = 0; t < G + 3 && G > 0; ++t)
@@ -632,42 +657,57 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         // ---- end of pass: publish z', clear the spare buffer, grid barrier ----
         {
             const int64_t tp = a.t0 + it;
-            TS *zout = zbuf + size_t((tp + 1) % 3) * mP + size_t(w0) * P;
-            TS *zsp = zbuf + size_t((tp + 2) % 3) * mP;
-            if (!is_ctl) {
-#pragma unroll
-                for (int sl = 0; sl < WPW; ++sl) {
-                    const int wl = warp * WPW + sl;
-                    if (wl < W_cta) {
-#pragma unroll
-                        for (int h = 0; h < H; ++h)
-                            atomic_add_vec<TS>(zout + size_t(wl) * P + (h * 32 + lane) * V, &acc[sl][h * V], V);
-                    }
-                }
-            }
-            for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x)
-                zsp[i] = TS(0);
             cur ^= 1;
-            if (it + 1 < a.iters) {
-                __syncthreads();
-                if (tid == 0) {
-                    __threadfence();
-                    red_release_add_u32(a.bar, 1u);
-                    const uint32_t target = uint32_t(it + 1) * gridDim.x + a.barrier_skew;
-                    if (ld_acquire_u32(a.bar) < target) {
-                        const uint64_t t_start = globaltimer_ns();
-                        while (ld_acquire_u32(a.bar) < target) {
-                            if (globaltimer_ns() - t_start > a.timeout_ns) {
-                                abort_flag = 1;
-                                abort_code = DEV_TIMEOUT_GRID;
-                                break;
-                            }
+            if (!a.det) {
+                TS *zout = zbuf + size_t((tp + 1) % 3) * mP + size_t(w0) * P;
+                TS *zsp = zbuf + size_t((tp + 2) % 3) * mP;
+                if (!is_ctl) {
+#pragma unroll
+                    for (int sl = 0; sl < WPW; ++sl) {
+                        const int wl = warp * WPW + sl;
+                        if (wl < W_cta) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+                                atomic_add_vec<TS>(zout + size_t(wl) * P + (h * 32 + lane) * V, &acc[sl][h * V], V);
                         }
                     }
-                    __threadfence();
                 }
-                if (__syncthreads_or(abort_flag)) goto abort_exit;
-                load_z(tp + 1);
+                for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x)
+                    zsp[i] = TS(0);
+                if (it + 1 < a.iters) {
+                    if (grid_sync()) goto abort_exit;
+                    load_z(tp + 1);
+                }
+            } else {
+                // deterministic: this cluster's partial z' for its workers, then
+                // (all partials visible) a fixed-order sum over the clusters
+                TS *zp = reinterpret_cast<TS *>(a.zpart) + size_t(cl) * mP + size_t(w0) * P;
+                if (!is_ctl) {
+#pragma unroll
+                    for (int sl = 0; sl < WPW; ++sl) {
+                        const int wl = warp * WPW + sl;
+                        if (wl < W_cta) {
+#pragma unroll
+                            for (int h = 0; h < H; ++h)
+#pragma unroll
+                                for (int v = 0; v < V; ++v)
+                                    __stcg(zp + size_t(wl) * P + (h * 32 + lane) * V + v, acc[sl][h * V + v]);
+                        }
+                    }
+                }
+                if (grid_sync()) goto abort_exit;
+                const TS *zpa = reinterpret_cast<const TS *>(a.zpart);
+                TS *zfull = zbuf + size_t((tp + 1) % 3) * mP;
+                const int ncl = int(gridDim.x) / cs;
+                for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x) {
+                    TS sum = TS(0);
+                    for (int c2 = 0; c2 < ncl; ++c2) sum += __ldcg(zpa + size_t(c2) * mP + i);
+                    zfull[i] = sum;
+                }
+                if (it + 1 < a.iters) {
+                    if (grid_sync()) goto abort_exit;
+                    load_z(tp + 1);
+                }
             }
         }
     }

@@ -272,6 +272,58 @@ __global__ void bsolve_kernel(const TS *z, const int64_t *row_start, const int32
     }
 }
 
+// ---- free residual monitor -------------------------------------------------------
+// Row block b of the residual of xbar: A_b xbar - rhs_b = D^{-1} R'^T (Q_b^T xbar - c_b)
+// with (D A_b)^T = Q_b R', R' = R2 R1 the two Cholesky factors, and
+// c_b = R'^{-T} D rhs_b.  While every x_i solves its block (App. A),
+// Q_b^T xbar - c_b = Q_b^T (xbar - x_b) = z_b, the coefficients the iteration
+// kernel already holds; so ||residual||^2 = sum_b ||D^{-1} R1^T R2^T z_b||^2, a
+// p x p product per block.  sums[0] += that sum.
+template <typename TS>
+__global__ void monitor_kernel(const TS *z, const int64_t *row_start, const int32_t *pcount, const double *dinv,
+                               const double *R1f, const double *R2f, int P, double *sums) {
+    extern __shared__ double sh[];  // v[P], w[P]
+    __shared__ double part[32];
+    const int b = blockIdx.x;
+    const int p = pcount[b];
+    const int64_t r0 = row_start[b];
+    const double *R1 = R1f + size_t(b) * P * P, *R2 = R2f + size_t(b) * P * P;
+    double *v = sh, *w = sh + P;
+    for (int c = threadIdx.x; c < P; c += blockDim.x) v[c] = c < p ? double(z[size_t(b) * P + c]) : 0.0;
+    __syncthreads();
+    // w = R2^T v: w[c] = sum_{r <= c} R2[r][c] v[r]
+    for (int c = threadIdx.x; c < P; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r <= c && r < p; ++r) s = fma(R2[size_t(r) * P + c], v[r], s);
+        w[c] = c < p ? s : 0.0;
+    }
+    __syncthreads();
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < p; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = 0; r <= c; ++r) s = fma(R1[size_t(r) * P + c], w[r], s);
+        const double res = s / dinv[r0 + c];
+        acc = fma(res, res, acc);
+    }
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < int(blockDim.x >> 5); ++i) t += part[i];
+        atomicAdd(sums, t);
+    }
+}
+
+// sums[0] += ||v||^2
+__global__ void sumsq_kernel(const double *v, int64_t count, double *sums) {
+    double acc = 0.0;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+        acc = fma(v[i], v[i], acc);
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) atomicAdd(sums, acc);
+}
+
 // ---- residual out = rhs - A x; sums += (||out||^2, ||rhs||^2) -----------------
 // One warp per row, RPW rows per warp, x staged through shared memory in
 // chunks shared by the CTA's warps.
@@ -481,6 +533,25 @@ cudaError_t launch_bsolve(const void *z, const int64_t *row_start_dev, const int
     else
         bsolve_kernel<float><<<unsigned(m), 256, sh, s>>>(static_cast<const float *>(z), row_start_dev, p_dev,
                                                          dinv, Rinv1, Rinv2, P, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_monitor(const void *z, int precision, const int64_t *row_start_dev, const int32_t *p_dev,
+                           const double *dinv, const double *R1, const double *R2, int m, int P, double *sums,
+                           cudaStream_t s) {
+    const size_t sh = sizeof(double) * 2 * P;
+    if (precision == 0)
+        monitor_kernel<double><<<m, 256, sh, s>>>(static_cast<const double *>(z), row_start_dev, p_dev, dinv, R1, R2, P,
+                                                  sums);
+    else
+        monitor_kernel<float><<<m, 256, sh, s>>>(static_cast<const float *>(z), row_start_dev, p_dev, dinv, R1, R2, P,
+                                                 sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq(const double *v, int64_t count, double *sums, cudaStream_t s) {
+    const unsigned grid = unsigned(std::min<int64_t>((count + 255) / 256, 1024));
+    sumsq_kernel<<<grid, 256, 0, s>>>(v, count, sums);
     return cudaGetLastError();
 }
 

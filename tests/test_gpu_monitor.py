@@ -1,0 +1,70 @@
+"""The free residual monitor (apc_monitor) against the FP64 residual, and
+apc_solve's use of it, through the C ABI.
+
+Every x_i solves its block (App. A), so block i's residual of xbar is
+D_i^{-1} R_i'^T Q_i^T (xbar - x_i), from the coefficients the iteration kernel
+keeps for its next pass.  Its error is set by the stored bases and by z: the
+FP32 products of n terms leave about sqrt(n) u ||xbar - x_i|| in z, a few 1e-6
+of ||b|| at these sizes, and FP64 about 1e-13."""
+import numpy as np
+import pytest
+
+from oracle import apc_oracle as O
+from paper_1708_01413_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _env():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1708_01413_gb300 import apc, build
+    build.build()
+    return apc, torch.device("cuda:0")
+
+
+@pytest.mark.parametrize("prec,rtol,atol", [("f64", 1e-8, 1e-13), ("f32", 1e-2, 1e-5)])
+def test_monitor_tracks_fp64_residual(prec, rtol, atol):
+    apc, dev = _env()
+    n, N, m = 1536, 1728, 9  # tall system, blocks of 192 rows
+    A, _, b = inputs.gaussian_system(n, 81, N=N)
+    offs = inputs.even_offsets(N, m)
+    bl = O.partition(A, b, offs)
+    lo, hi = O.mu_bounds([O.block_qr(Ai)[0] for Ai, _ in bl])
+    g, e, _ = O.optimal_params(lo, hi)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    r2 = torch.tensor(np.random.default_rng(3).standard_normal(N), device=dev)
+    seen = []
+    for rhs in (None, r2):  # the stored b, then another right-hand side (as in refinement sweeps)
+        ctx.reset(rhs)
+        for k in (0, 1, 10, 50, 200, 400):
+            if k:
+                ctx.iterate(g, e, k)
+            mon = ctx.monitor()
+            res = ctx.residual(ctx.xbar(), rhs=rhs)
+            assert abs(mon - res) <= rtol * res + atol, (prec, k, mon, res)
+            seen.append(res)
+    assert min(seen) < 1e-2 * max(seen)  # the checks spanned a real decrease of the residual
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_solve_checks_with_the_monitor(prec):
+    # FP32/FP64: checks by the monitor, an FP64 residual only to confirm;
+    # BF16: FP64 residuals; every mode ends on an FP64 residual below tol
+    apc, dev = _env()
+    n, N, m = 1024, 1152, 9
+    A, _, b = inputs.gaussian_system(n, 82, N=N)
+    offs = inputs.even_offsets(N, m)
+    bl = O.partition(A, b, offs)
+    lo, hi = O.mu_bounds([O.block_qr(Ai)[0] for Ai, _ in bl])
+    g, e, _ = O.optimal_params(lo, hi)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    tol = 1e-10 if prec == "f64" else 1e-9
+    x, st = ctx.solve(g, e, tol=tol, max_iters=200000, check_every=20, refine=prec != "f64")
+    assert O.relative_residual(A, b, x.cpu().numpy()) <= tol
+    if prec == "bf16":
+        assert st["monitor_checks"] == 0
+    else:
+        assert st["monitor_checks"] > 0
+        assert st["residual_checks"] < st["monitor_checks"]
