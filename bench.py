@@ -460,6 +460,8 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
     info = bt.info()
     bt.set_params([1.0] * nsys, [1.0] * nsys)  # in S for every system; the cost does not depend on them
     bt.reset()
+    tiles, ms_tuned, ms_default = bt.autotune(iters=5, reps=2)  # the project's tile tuner (cached per key)
+    bt.reset()
     bt.iterate(iters)
     torch.cuda.synchronize()
     ev = [(_ev(), _ev()) for _ in range(reps)]
@@ -501,6 +503,8 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
                         f"A = G + 0.5 sqrt(n) I, blocks p_i ~ U{{16..128}}, k = {k}, BF16 bases",
             "iter_per_s": 1.0 / sec, "ms_per_iter": sec * 1e3, "rhs_iter_per_s": nsys * k / sec,
             "iters_per_launch": iters, "launches": reps, "setup_s": round(setup_s, 3), "grid": info["grid"],
+            "tiles": {"rows_a": tiles[0], "cols_b": tiles[1], "prefetch": tiles[2],
+                      "tuner_ms_per_iter": ms_tuned, "default_ms_per_iter": ms_default},
             "clocks": clk.summary(),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "algorithmic_bytes_per_iter": alg, "traffic_model_padded_bytes_per_iter": padded,
@@ -533,6 +537,13 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3):
     offs = inputs.even_offsets(n, m)
     gam, eta = 1.0, 1.5
     out = {"workload": f"Gaussian {n} x {n}, m = {m} blocks of {n // m}, k = {k}, T = {T}"}
+    # the tile tuner on the same single system (one-system batch, k columns)
+    bt = apc.apc_batch_setup([A], [B], [offs])
+    bt.set_params([gam], [eta])
+    bt.reset()
+    tiles, ms_tuned, ms_default = bt.autotune(iters=20, reps=2)
+    out["tuner"] = {"tiles": list(tiles), "ms_per_iter": ms_tuned, "default_256_512_ms_per_iter": ms_default}
+    bt.close()
     for prec in ("bf16", "f32"):
         ctx = apc.apc_setup(A, B[:, 0].contiguous(), offs, precision=prec)
         try:

@@ -31,6 +31,7 @@ EXPORTED = (
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
     "apc_residual_noalloc", "apc_forward_rhs", "apc_backward_rhs", "apc_batch_forward", "apc_batch_backward",
     "apc_monitor", "apc_set_deterministic", "apc_state_bytes", "apc_export_state", "apc_import_state",
+    "apc_batch_set_tiles", "apc_batch_get_tiles", "apc_batch_autotune",
 )
 
 
@@ -90,6 +91,10 @@ def lib() -> C.CDLL:
     L.apc_import_state.argtypes = [vp, vp, C.c_size_t, vp]
     L.apc_backward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
     L.apc_batch_forward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
+    L.apc_batch_set_tiles.argtypes = [vp, i32, i32, i32]
+    L.apc_batch_get_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
+    L.apc_batch_autotune.argtypes = [vp, i64, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl),
+                                     C.POINTER(dbl), vp]
     L.apc_batch_backward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
     L.apc_last_error.argtypes = [vp]
     L.apc_last_error.restype = C.c_char_p
@@ -480,12 +485,13 @@ def _check_batch(rc: int, handle=None):
 class Batch:
     """Owns an ``apc_batch``: independent square systems advanced together."""
 
-    def __init__(self, handle: C.c_void_p, device, n, k, B):
+    def __init__(self, handle: C.c_void_p, device, n, k, B, key=None):
         self.handle = handle
         self.device = device
         self.n = list(n)
         self.k = k
         self._B = B  # the caller's right-hand sides (kept alive for reset)
+        self.key = key  # tile-cache key (tile_cache_key)
 
     def __del__(self):
         try:
@@ -557,6 +563,29 @@ class Batch:
         _check_batch(lib().apc_batch_set_test_hooks(self.handle, int(grid_barrier_skew), float(timeout_s)),
                      self.handle)
 
+    def set_tiles(self, rows_a: int, cols_b: int, prefetch: int):
+        """Work-unit shape of the persistent kernel (apc_batch_set_tiles)."""
+        _check_batch(lib().apc_batch_set_tiles(self.handle, int(rows_a), int(cols_b), int(prefetch)), self.handle)
+
+    def tiles(self):
+        ra, cb, pf = C.c_int32(), C.c_int32(), C.c_int32()
+        _check_batch(lib().apc_batch_get_tiles(self.handle, C.byref(ra), C.byref(cb), C.byref(pf)), self.handle)
+        return ra.value, cb.value, pf.value
+
+    def autotune(self, iters: int = 5, reps: int = 3, cache: str | None = None, stream=None):
+        """Run the tile tuner (apc_batch_autotune) and store its choice in the
+        tile cache under this batch's key; the iteration state must be reset
+        afterwards.  Returns (tiles, ms per iteration tuned, ms default)."""
+        ra, cb, pf = C.c_int32(), C.c_int32(), C.c_int32()
+        best, dflt = C.c_double(), C.c_double()
+        with _device(self.device):
+            _check_batch(lib().apc_batch_autotune(self.handle, int(iters), int(reps), C.byref(ra), C.byref(cb),
+                                                  C.byref(pf), C.byref(best), C.byref(dflt), _stream(stream)),
+                         self.handle)
+        tiles = (ra.value, cb.value, pf.value)
+        store_tiles(self.key, tiles, cache)
+        return tiles, best.value, dflt.value
+
     def forward(self, T: int, B=None, stream=None):
         """Reset (with new right-hand sides B, one n_s x k tensor per system, or
         the stored ones), T iterations and every system's xbar(T), in one call
@@ -602,10 +631,52 @@ def _batch_rhs(B, n, k):
     return B.contiguous()
 
 
-def apc_batch_setup(As, Bs, row_offsets, timeout_s=0.0, stream=None) -> Batch:
+TILE_CACHE = os.environ.get("APC_TILE_CACHE", os.path.join(HERE, "_build", "tile_cache.json"))
+
+
+def tile_cache_key(ns, block_sizes, k, sms) -> str:
+    """Key of the tile cache: histograms of the systems' sizes n and of the
+    block sizes p (power-of-two buckets), the right-hand sides and the SM count."""
+    import collections
+    hn = collections.Counter(int(n).bit_length() for n in ns)
+    hp = collections.Counter(int(p).bit_length() for p in block_sizes)
+    fmt = lambda h: ",".join(f"{b}:{h[b]}" for b in sorted(h))  # noqa: E731
+    return f"n[{fmt(hn)}]|p[{fmt(hp)}]|k{int(k)}|sm{int(sms)}"
+
+
+def load_tiles(key, cache=None):
+    import json
+    path = cache or TILE_CACHE
+    try:
+        with open(path) as fh:
+            v = json.load(fh).get(key)
+        return tuple(int(x) for x in v) if v else None
+    except (OSError, ValueError):
+        return None
+
+
+def store_tiles(key, tiles, cache=None):
+    import json
+    path = cache or TILE_CACHE
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        d = {}
+    d[key] = [int(x) for x in tiles]
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def apc_batch_setup(As, Bs, row_offsets, timeout_s=0.0, stream=None, tiles="cache", cache=None) -> Batch:
     """Factor every system: As[s] an n_s x n_s FP64 CUDA tensor, Bs[s] its
     n_s x k right-hand sides (k equal for all systems, <= 32), row_offsets[s]
-    its m_s + 1 block offsets."""
+    its m_s + 1 block offsets.  ``tiles``: "cache" (the tuner's stored choice
+    for this batch's key, else the default shape), "default", or a tuple
+    (rows_a, cols_b, prefetch)."""
     import numpy as np
     import torch
     nsys = len(As)
@@ -632,4 +703,10 @@ def apc_batch_setup(As, Bs, row_offsets, timeout_s=0.0, stream=None) -> Batch:
                                    o_arr.ctypes.data_as(C.POINTER(C.c_int64)), a_arr, b_arr, k, C.byref(opt),
                                    _stream(stream))
     _check_batch(rc, None)
-    return Batch(h, As[0].device, ns, k, Bs)
+    sms = torch.cuda.get_device_properties(As[0].device).multi_processor_count
+    key = tile_cache_key(ns, [int(o[i + 1] - o[i]) for o in offs for i in range(len(o) - 1)], k, sms)
+    bt = Batch(h, As[0].device, ns, k, Bs, key)
+    chosen = load_tiles(key, cache) if tiles == "cache" else (None if tiles == "default" else tuple(tiles))
+    if chosen:
+        bt.set_tiles(*chosen)
+    return bt

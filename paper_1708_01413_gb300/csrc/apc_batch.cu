@@ -78,9 +78,10 @@ constexpr int kConsumerWarps = 8;
 constexpr int kProducerWarp = kConsumerWarps;       // issues the bulk copies
 constexpr int kMmaWarp = kConsumerWarps + 1;        // issues the tensor-core instructions
 constexpr int kThreads = 32 * (kConsumerWarps + 2);
-constexpr int kTileRows = 256;   // rows of a sweep-A unit (32 per consumer warp)
+constexpr int kTileRows = 256;   // rows of a basis storage tile (the largest sweep-A unit; 32 per consumer warp)
+constexpr int kXRows = 128;      // rows of an x_i storage block (the smallest sweep-A unit)
 constexpr int kWin = 64;         // basis columns per sweep-A window (one 128-byte row)
-constexpr int kColsB = 512;      // columns of a sweep-B unit (64 per consumer warp)
+constexpr int kColsB = 512;      // columns of the largest sweep-B unit (64 per consumer warp)
 constexpr int kRowsStageB = 32;  // rows per sweep-B stage
 constexpr int kQSlots = 4, kXSlots = 2;
 constexpr int kUQ = 4;           // depth of the queue of claimed units (producer -> consumers)
@@ -88,8 +89,7 @@ constexpr int kPlanesA = 2, kPlanesB = 3;
 constexpr int kSlotQBytes = kTileRows * kWin * 2;  // 32 KB: 256 x 64 or 8 x (32 x 64) BF16
 constexpr int kSlotZBytes = 8192;                  // operand planes of one stage
 constexpr int kSlotBytes = kSlotQBytes + kSlotZBytes;
-constexpr int kXPad = 0;                           // FP32 padding per right-hand-side row of an x_i tile
-constexpr int kXSlotBytes = 32 * (kTileRows + kXPad) * 4;
+constexpr int kXSlotBytes = 32 * kTileRows * 4;    // x_i of one machine: two [32][128] FP32 blocks
 constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
 // mbarriers: Q slots full/empty, x slots full/empty, unit queue full/empty,
 // sweep-A accumulators full/free (two buffers), sweep-B accumulator full/free,
@@ -101,7 +101,7 @@ constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, 
 
 struct SysDesc {
     const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
-    float *X;                // tile-major x_i blocks (see x_block)
+    float *X;                // x_i in blocks of 128 rows (see x_block)
     float2 *Xb;              // [kp][npad]  master estimate, double-float
     uint8_t *Xop;            // xbar' planes, B operand of sweep B (see op_offset), npad x 3kp BF16
     uint8_t *Zop;            // z planes, B operand of sweep A (see op_offset), Cq x 2kp BF16
@@ -127,6 +127,9 @@ struct BatchArgs {
     int init;
     int hb;              // 1: distributed-preconditioned heavy ball instead of APC
     int adj;             // 1: reverse sweep through `iters` steps (apc_batch_backward)
+    int rowsA;           // rows of a sweep-A unit: 128 or 256
+    int colsB;           // columns of a sweep-B unit: 128, 256 or 512
+    int prefetch;        // sweep A: L2 prefetch distance in windows / machines (0..8)
     uint32_t barrier_skew;  // test hook: added to every cross-CTA wait target (0 = normal)
     uint32_t *bar;          // grid barrier after the initialisation (zero at launch)
     int *err;
@@ -139,9 +142,10 @@ __host__ __device__ __forceinline__ int tile_rows(int npad, int t) { return min(
 __host__ __device__ __forceinline__ size_t q_block(int Cq, int npad, int t, int w) {
     return size_t(t) * kTileRows * Cq + size_t(w) * tile_rows(npad, t) * kWin;
 }
-// first element of machine i's x_i block in tile t: [kp][tile_rows + kXPad] FP32
-__host__ __device__ __forceinline__ size_t x_block(int m, int kp, int npad, int t, int i) {
-    return size_t(t) * m * kp * (kTileRows + kXPad) + size_t(i) * kp * (tile_rows(npad, t) + kXPad);
+// first element of machine i's x_i block for rows 128 u .. 128 u + 127:
+// [kp][128] FP32 (the last block of a system padded to 128 rows with zeros)
+__host__ __device__ __forceinline__ size_t x_block(int m, int kp, int u, int i) {
+    return (size_t(u) * m + i) * kp * kXRows;
 }
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -317,36 +321,44 @@ __device__ __forceinline__ bool acquire_slot(const Ring &R, uint64_t *empty, int
 
 // ---- sweep A ---------------------------------------------------------------------
 template <int MT>
-__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, bool no_x,
+__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, int rowsA, int pf, bool no_x,
                                  uint64_t policy) {
     constexpr int KP = 16 * MT;
-    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    // the unit's rows within their 256-row basis tile (the window blocks are
+    // [tile rows][64] row-major, so any 128-row part of one is contiguous)
+    const int t = row0 / kTileRows, ro = row0 - t * kTileRows;
+    const int rows = min(rowsA, d.npad - row0);
     const int nwin = d.Cq / kWin;
     const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = kPlanesA * KP * 128;
-    const uint32_t xbytes = uint32_t(KP) * (rows + kXPad) * 4;
+    const int u0 = row0 / kXRows, nxb = (rows + kXRows - 1) / kXRows;  // x_i blocks of 128 rows per machine
+    const uint32_t xblk = uint32_t(KP) * kXRows * 4;
+    auto qsrc = [&](int w) { return d.Q + q_block(d.Cq, d.npad, t, w) + size_t(ro) * kWin; };
     int pi = 0;  // next machine whose x_i tile is due
-    // L2 prefetch runs kPrefetch windows / machines ahead of the shared-memory
-    // ring (measured on 256 systems: 2 is 1.5 % faster than 4, 8 is 13 % slower,
-    // none 4 % slower; an L2 prefetch in sweep B made it 40 % slower)
-    constexpr int kPrefetch = 2;
-    for (int w = 0; w < min(kPrefetch, nwin); ++w) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w), qbytes);
+    // L2 prefetch runs `pf` windows / machines ahead of the shared-memory ring
+    // (measured on 256 systems with 256-row units: 2 is 1.5 % faster than 4, 8
+    // is 13 % slower, none 4 % slower; an L2 prefetch in sweep B made it 40 %
+    // slower); the tile tuner may pick another distance
+    for (int w = 0; w < min(pf, nwin); ++w) prefetch_l2(qsrc(w), qbytes);
     if (!no_x)
-        for (int j = 0; j < min(kPrefetch, d.m); ++j) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, j), xbytes);
+        for (int i = 0; i < min(pf, d.m); ++i)
+            for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, i), xblk);
     for (int w = 0; w < nwin; ++w) {
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
         mbar_arrive_expect_tx(&R.full[s], qbytes + zbytes);
-        tma_load_1d(R.qslot(s), d.Q + q_block(d.Cq, d.npad, t, w), qbytes, &R.full[s], policy);
+        tma_load_1d(R.qslot(s), qsrc(w), qbytes, &R.full[s], policy);
         tma_load_1d(R.qslot(s) + kSlotQBytes, d.Zop + size_t(w) * zbytes, zbytes, &R.full[s], policy);
-        if (w + kPrefetch < nwin) prefetch_l2(d.Q + q_block(d.Cq, d.npad, t, w + kPrefetch), qbytes);
+        if (w + pf < nwin) prefetch_l2(qsrc(w + pf), qbytes);
         ++cur.q;
         // x_i tiles of the machines whose last chunk lies in this window
         while (!no_x && pi < d.m && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
             const uint32_t xs = cur.x % kXSlots;
             if (!acquire_slot(R, R.xempty, kXSlots, cur.x)) return;
-            mbar_arrive_expect_tx(&R.xfull[xs], xbytes);
-            tma_load_1d(R.xslot(xs), d.X + x_block(d.m, KP, d.npad, t, pi), xbytes, &R.xfull[xs], policy);
-            if (pi + kPrefetch < d.m) prefetch_l2(d.X + x_block(d.m, KP, d.npad, t, pi + kPrefetch), xbytes);
+            mbar_arrive_expect_tx(&R.xfull[xs], uint32_t(nxb) * xblk);
+            for (int j = 0; j < nxb; ++j)
+                tma_load_1d(R.xslot(xs) + j * xblk, d.X + x_block(d.m, KP, u0 + j, pi), xblk, &R.xfull[xs], policy);
+            if (pi + pf < d.m)
+                for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, pi + pf), xblk);
             ++cur.x;
             ++pi;
         }
@@ -362,10 +374,10 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
 // Heavy ball: one accumulation over every machine of the tile.
 template <int MT>
 __device__ void sweep_a_mma(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
-                            const SysDesc &d, int row0, bool hb, uint32_t tmem) {
+                            const SysDesc &d, int row0, int rowsA, bool hb, uint32_t tmem) {
     constexpr int NA = kPlanesA * 16 * MT;
     constexpr uint32_t idesc = instr_desc(NA, 0);
-    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    const int rows = min(rowsA, d.npad - row0);
     const int nmt = rows > 128 ? 2 : 1;
     const int nwin = d.Cq / kWin, nchunk = d.C / 16;
     int i = 0, iend = __ldg(d.coloff + 1) >> 4;
@@ -429,12 +441,12 @@ __device__ void store_xop(const SysDesc &d, int64_t row, const float (&xo)[16 * 
 // the step's row update of (ell, lbar) and the planes of the next mu.
 template <int MT, bool kAdj>
 __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
-                                 const SysDesc &d, int row0, bool init, bool hb, float gh, float gl, uint32_t tmem,
-                                 bool last) {
+                                 const SysDesc &d, int row0, int rowsA, bool init, bool hb, float gh, float gl,
+                                 uint32_t tmem, bool last) {
     constexpr int KP = 16 * MT, NA = kPlanesA * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = warp >> 2, quad = warp & 3;
-    const int t = row0 / kTileRows, rows = tile_rows(d.npad, t);
+    const int rows = min(rowsA, d.npad - row0);
     const int r = 128 * h + 32 * quad + lane;         // row within the tile
     const bool wact = 128 * h + 32 * quad < rows;     // rows is a multiple of 32: warp-uniform
     const int64_t grow = int64_t(row0) + r;           // row within the system
@@ -481,19 +493,17 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
             sx = smem_u32(R.xslot(xs));
         }
         if (wact) {
-            // the x_i tile's stride, re-materialised per machine so that the
-            // compiler keeps no per-right-hand-side offsets live across machines
-            uint32_t rs;
-            asm volatile("mov.b32 %0, %1;" : "=r"(rs) : "r"(uint32_t(rows) * 4u));
-            const uint32_t sxr = sx + uint32_t(r) * 4u;
-            char *xg = reinterpret_cast<char *>(d.X + x_block(d.m, KP, d.npad, t, i) + r);
+            // the x_i tile holds [kp][128] blocks of 128 rows: the row's value
+            // for right-hand side q sits 512 q bytes after its first one
+            const uint32_t sxr = sx + uint32_t(h) * uint32_t(KP * kXRows * 4) + uint32_t(r & (kXRows - 1)) * 4u;
+            float *xg = d.X + x_block(d.m, KP, (row0 >> 7) + h, i) + (r & (kXRows - 1));
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
-                const float xo = init ? 0.0f : lds_f32(sxr + uint32_t(q) * rs);
+                const float xo = init ? 0.0f : lds_f32(sxr + uint32_t(q) * (kXRows * 4));
                 const float v = ((xbh[q] - xo) + xbl[q]) - W[q];
                 const float xn = upd_exact(xo, gh, gl, v);
                 S[q] += xn;
-                __stcg(reinterpret_cast<float *>(xg + uint32_t(q) * rs), xn);
+                __stcg(xg + q * kXRows, xn);
             }
         }
         if (!init) {
@@ -564,8 +574,9 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
 
 // ---- sweep B -----------------------------------------------------------------------
 template <int MT>
-__device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, uint64_t policy) {
-    const int nwin = min(kColsB, d.Cq - col0) / kWin;
+__device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, int colsB,
+                                 uint64_t policy) {
+    const int nwin = min(colsB, d.Cq - col0) / kWin;
     const uint32_t xbytes = kPlanesB * 16 * MT * 64;  // 32 rows
     for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
         const uint32_t s = cur.q % kQSlots;
@@ -640,10 +651,10 @@ __device__ void store_v(const SysDesc &d, int col, const float (&Y)[16 * MT], bo
 // per unit and are reused after they release them.
 template <int MT>
 __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree,
-                            const SysDesc &d, int col0, uint32_t tmem) {
+                            const SysDesc &d, int col0, int colsB, uint32_t tmem) {
     constexpr int NB = kPlanesB * 16 * MT;
     constexpr uint32_t idesc = instr_desc(NB, 1);
-    const int nmt = (min(kColsB, d.Cq - col0) + 127) / 128;
+    const int nmt = (min(colsB, d.Cq - col0) + 127) / 128;
     if (ubc > 0 && !R.wait(bfree, (ubc - 1) & 1)) return;
     tc_fence_after();
     bool first = true;
@@ -672,10 +683,10 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
 // (reverse sweep: v = Y, see store_v).
 template <int MT, bool kAdj>
 __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree, const SysDesc &d,
-                                 int col0, uint32_t tmem, bool fin) {
+                                 int col0, int colsB, uint32_t tmem, bool fin) {
     constexpr int KP = 16 * MT, NB = kPlanesB * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3;
-    const int ncols = min(kColsB, d.Cq - col0);
+    const int ncols = min(colsB, d.Cq - col0);
     if (!R.wait(bfull, ubc & 1)) return;
     tc_fence_after();
     const uint32_t tl = tmem + (uint32_t(32 * quad) << 16);
@@ -886,8 +897,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 ++uk;
                 if (g < 0) return;
                 const SysDesc &d = a.sys[u.U.x];
-                if (u.is_a) sweep_a_producer<MT>(R, cur, d, u.U.y, u.init || u.hb, policy);
-                else sweep_b_producer<MT>(R, cur, d, u.U.y, policy);
+                if (u.is_a) sweep_a_producer<MT>(R, cur, d, u.U.y, a.rowsA, a.prefetch, u.init || u.hb, policy);
+                else sweep_b_producer<MT>(R, cur, d, u.U.y, a.colsB, policy);
             }
         } else if (mma_warp) {
             if (lane != 0) return;
@@ -913,8 +924,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                     tc_fence_after();
                 }
                 prev = u.is_a ? 0 : 1;
-                if (u.is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, d, u.U.y, u.hb, tmem);
-                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, d, u.U.y, tmem);
+                if (u.is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, d, u.U.y, a.rowsA, u.hb, tmem);
+                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, d, u.U.y, a.colsB, tmem);
             }
         } else {
             for (;;) {
@@ -928,10 +939,10 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 const Unit u = decode(g);
                 const SysDesc &d = a.sys[u.U.x];
                 if (u.is_a)
-                    sweep_a_consumer<MT, kAdj>(R, cur, mc, dfull, dfree, d, u.U.y, u.init, u.hb,
+                    sweep_a_consumer<MT, kAdj>(R, cur, mc, dfull, dfree, d, u.U.y, a.rowsA, u.init, u.hb,
                                                u.init ? 1.0f : d.g_hi, u.init ? 0.0f : d.g_lo, tmem, u.edge);
                 else
-                    sweep_b_consumer<MT, kAdj>(R, ubc, bfull, bfree, d, u.U.y, tmem, u.edge);
+                    sweep_b_consumer<MT, kAdj>(R, ubc, bfull, bfree, d, u.U.y, a.colsB, tmem, u.edge);
                 __syncwarp();
                 if (*reinterpret_cast<volatile int *>(&abort_flag)) return;
                 // the unit's global writes are read by other CTAs (bulk
@@ -951,7 +962,7 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
             for (int u = blockIdx.x; u < a.nB; u += gridDim.x) {
                 const int2 U = a.unitsB[u];
                 const SysDesc &d = a.sys[U.x];
-                const int ncols = min(kColsB, d.Cq - U.y);
+                const int ncols = min(a.colsB, d.Cq - U.y);
                 for (int hh = 0; hh < 2; ++hh) {
                     const int cl = 128 * ((warp >> 2) + 2 * hh) + 32 * (warp & 3);
                     if (cl < ncols) {
@@ -1049,8 +1060,7 @@ __global__ void x_out_kernel(const float *X, int64_t n, int npad, int m, int kp,
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
         const int j = int(i / k);
         const int r = int(i - int64_t(j) * k);
-        const int t = j / kTileRows;
-        const size_t off = x_block(m, kp, npad, t, worker) + size_t(r) * (tile_rows(npad, t) + kXPad) + j % kTileRows;
+        const size_t off = x_block(m, kp, j / kXRows, worker) + size_t(r) * kXRows + j % kXRows;
         out[int64_t(j) * ldx + r] = double(X[off]);
     }
 }
@@ -1115,6 +1125,7 @@ void split_f64(double v, float &hi, float &lo) {
 struct apc_batch {
     int device = 0, k = 1, kp = 16, MT = 1, nsys = 0, grid = 0;
     int units_a = 0, units_b = 0;
+    int rowsA = 256, colsB = 512, prefetch = 2;  // unit shape (apc_batch_set_tiles)
     std::vector<apc_ctx *> ctx;
     std::vector<SysDesc> desc;
     std::vector<int64_t> n;
@@ -1203,6 +1214,9 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s, bool adj = fal
     a.init = init;
     a.hb = init || adj ? 0 : b->method;
     a.adj = adj ? 1 : 0;
+    a.rowsA = b->rowsA;
+    a.colsB = b->colsB;
+    a.prefetch = b->prefetch;
     a.barrier_skew = b->barrier_skew;
     a.bar = reinterpret_cast<uint32_t *>(b->ctr);
     a.err = b->err;
@@ -1269,6 +1283,29 @@ int run_graph(apc_batch *b, int64_t iters, bool adj, cudaStream_t s) {
     }
     BCK(b, cudaGraphLaunch(exec, s));
     return check_err(b, s);
+}
+
+// Work lists for the current unit shape, system-major: the systems with the
+// most bytes first, each system's units together (stable sort on the
+// system's bytes); the per-system unit counts go to the descriptors.
+int build_units(apc_batch *b, cudaStream_t s) {
+    std::vector<std::pair<double, int2>> ia, ib;
+    for (int sys = 0; sys < b->nsys; ++sys) {
+        SysDesc &d = b->desc[sys];
+        d.nuA = (d.npad + b->rowsA - 1) / b->rowsA;
+        d.nuB = (d.Cq + b->colsB - 1) / b->colsB;
+        const double bytes = double(d.npad) * (4.0 * d.Cq + 8.0 * d.m * b->kp);
+        for (int r0 = 0; r0 < d.npad; r0 += b->rowsA) ia.push_back({bytes, make_int2(sys, r0)});
+        for (int c0 = 0; c0 < d.Cq; c0 += b->colsB) ib.push_back({bytes, make_int2(sys, c0)});
+    }
+    const std::vector<int2> ua = by_key_desc(ia), ub = by_key_desc(ib);
+    b->units_a = int(ua.size());
+    b->units_b = int(ub.size());
+    BCK(b, cudaMemcpyAsync(b->d_unitsA, ua.data(), sizeof(int2) * ua.size(), cudaMemcpyHostToDevice, s));
+    BCK(b, cudaMemcpyAsync(b->d_unitsB, ub.data(), sizeof(int2) * ub.size(), cudaMemcpyHostToDevice, s));
+    BCK(b, cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(SysDesc) * b->nsys, cudaMemcpyHostToDevice, s));
+    BCK(b, cudaStreamSynchronize(s));
+    return APC_OK;
 }
 
 int compute_coefficients(apc_batch *b, int sys, cudaStream_t s) {
@@ -1356,7 +1393,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         const int C = co[m];
         const int Cq = (C + kWin - 1) / kWin * kWin;
         const int64_t npad = (n + 31) / 32 * 32;
-        const int ntiles = int((npad + kTileRows - 1) / kTileRows);
+        const int nxblocks = int((npad + kXRows - 1) / kXRows);
         std::vector<int> colblk(Cq / 16, -1);
         for (int i = 0; i < m; ++i)
             for (int g16 = co[i] / 16; g16 < co[i + 1] / 16; ++g16) colblk[g16] = i;
@@ -1365,7 +1402,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         d.m = m;
         d.Cq = Cq;
         d.C = C;
-        const size_t x_elems = x_block(m, kp, int(npad), ntiles, 0);
+        const size_t x_elems = x_block(m, kp, nxblocks, 0);
         int *d_co = nullptr, *d_cb = nullptr;
         __nv_bfloat16 *Q = nullptr;
         float *Cf = nullptr;
@@ -1448,25 +1485,15 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         return bail(APC_ERR_LAUNCH);
     }
     b->grid = sms;
-    // work lists, system-major: the systems with the most bytes first, each
-    // system's units together (stable sort on the system's bytes)
-    std::vector<std::pair<double, int2>> ia, ib;
-    for (int sys = 0; sys < nsys; ++sys) {
-        SysDesc &d = b->desc[sys];
-        d.nuA = (d.npad + kTileRows - 1) / kTileRows;
-        d.nuB = (d.Cq + kColsB - 1) / kColsB;
-        const double bytes = double(d.npad) * (4.0 * d.Cq + 8.0 * d.m * kp);
-        for (int r0 = 0; r0 < d.npad; r0 += kTileRows) ia.push_back({bytes, make_int2(sys, r0)});
-        for (int c0 = 0; c0 < d.Cq; c0 += kColsB) ib.push_back({bytes, make_int2(sys, c0)});
+    // work lists, sized for the smallest units (the tile tuner may pick them)
+    size_t max_a = 0, max_b = 0;
+    for (const SysDesc &d : b->desc) {
+        max_a += size_t((d.npad + kXRows - 1) / kXRows);
+        max_b += size_t((d.Cq + 127) / 128);
     }
-    const std::vector<int2> ua = by_key_desc(ia), ub = by_key_desc(ib);
-    b->units_a = int(ua.size());
-    b->units_b = int(ub.size());
-    if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * ua.size())) ||
-        (rc = balloc(b, &b->d_unitsB, sizeof(int2) * ub.size())))
+    if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * max_a)) || (rc = balloc(b, &b->d_unitsB, sizeof(int2) * max_b)))
         return bail(rc);
-    cudaMemcpyAsync(b->d_unitsA, ua.data(), sizeof(int2) * ua.size(), cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(b->d_unitsB, ub.data(), sizeof(int2) * ub.size(), cudaMemcpyHostToDevice, s);
+    if ((rc = build_units(b, s)) != APC_OK) return bail(rc);
     cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         bfail(b, APC_ERR_CUDA, "set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1547,6 +1574,84 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     if (!b->params_set) return bfail(b, APC_ERR_PARAMS, "apc_batch_set_params must precede apc_batch_iterate");
     if (!b->reset_done) return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_reset must precede apc_batch_iterate");
     return run_graph(b, iters, false, static_cast<cudaStream_t>(stream));
+}
+
+int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch) {
+    if (!b) return bfail(b, APC_ERR_INVALID_ARG, "NULL batch");
+    if ((rows_a != kXRows && rows_a != kTileRows) || (cols_b != 128 && cols_b != 256 && cols_b != kColsB) || prefetch < 0 ||
+        prefetch > 8)
+        return bfail(b, APC_ERR_INVALID_ARG, "tiles: rows_a in {128, 256}, cols_b in {128, 256, 512}, prefetch 0..8");
+    if (rows_a == b->rowsA && cols_b == b->colsB && prefetch == b->prefetch) return APC_OK;
+    BCK(b, cudaDeviceSynchronize());  // no launch may still read the work lists
+    b->rowsA = rows_a;
+    b->colsB = cols_b;
+    b->prefetch = prefetch;
+    for (cudaGraphExec_t *g : {&b->graph, &b->graph_adj})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+    return build_units(b, nullptr);
+}
+
+int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch) {
+    if (!b) return APC_ERR_INVALID_ARG;
+    if (rows_a) *rows_a = b->rowsA;
+    if (cols_b) *cols_b = b->colsB;
+    if (prefetch) *prefetch = b->prefetch;
+    return APC_OK;
+}
+
+int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_a, int32_t *cols_b,
+                       int32_t *prefetch, double *ms_best, double *ms_default, void *stream) {
+    if (!b || iters < 1 || reps < 1) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
+    if (!b->params_set || !b->reset_done)
+        return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_set_params and apc_batch_reset must precede the tuning");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {2, 0, 1, 4};
+    const int d_a = b->rowsA, d_b = b->colsB, d_p = b->prefetch;
+    int best_a = d_a, best_b = d_b, best_p = d_p;
+    double best = 1e300, dflt = -1.0;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    int rc = APC_OK;
+    for (int ra : cand_a)
+        for (int cb : cand_b)
+            for (int pf : cand_p) {
+                if ((rc = apc_batch_set_tiles(b, ra, cb, pf)) != APC_OK) break;
+                if ((rc = run_graph(b, iters, false, s)) != APC_OK) break;  // capture and warm-up
+                if (cudaEventRecord(e0, s) != cudaSuccess) { rc = APC_ERR_CUDA; break; }
+                for (int r = 0; r < reps && rc == APC_OK; ++r)
+                    if (cudaGraphLaunch(b->graph, s) != cudaSuccess) rc = APC_ERR_CUDA;
+                if (rc != APC_OK || cudaEventRecord(e1, s) != cudaSuccess) { rc = APC_ERR_CUDA; break; }
+                if ((rc = check_err(b, s)) != APC_OK) break;
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                const double per = double(ms) / double(reps * iters);
+                if (ra == d_a && cb == d_b && pf == d_p) dflt = per;
+                if (per < best) {
+                    best = per;
+                    best_a = ra;
+                    best_b = cb;
+                    best_p = pf;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != APC_OK) {
+        cudaGetLastError();
+        apc_batch_set_tiles(b, d_a, d_b, d_p);
+        return rc == APC_ERR_CUDA ? bfail(b, rc, "tuning launch failed") : rc;
+    }
+    if ((rc = apc_batch_set_tiles(b, best_a, best_b, best_p)) != APC_OK) return rc;
+    b->reset_done = false;  // the tuning advanced the iteration state
+    if (rows_a) *rows_a = best_a;
+    if (cols_b) *cols_b = best_b;
+    if (prefetch) *prefetch = best_p;
+    if (ms_best) *ms_best = best;
+    if (ms_default) *ms_default = dflt;
+    return APC_OK;
 }
 
 int apc_batch_forward(apc_batch *b, const double *const *B_dev_host, int64_t T, double *const *X_dev_host,
@@ -1701,6 +1806,9 @@ int multi_rhs_batch(apc_ctx *c, int64_t k, double gamma, double eta, cudaStream_
             return cfail(c, rc, "%s", apc_batch_last_error(nullptr));
         }
         c->mrhs_k = int(k);
+        // one system: the smallest units give the most units to the SMs
+        const int rc2 = apc_batch_set_tiles(c->mrhs, 128, 128, 2);
+        if (rc2 != APC_OK) return cfail(c, rc2, "%s", apc_batch_last_error(c->mrhs));
     }
     const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);
     if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));

@@ -70,6 +70,10 @@ constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps) * 32;
 void *iter_kernel_f64(int cpl, int wpw, bool apc, int rg);
 void *iter_kernel_f32(int cpl, int wpw, bool apc, int rg);
 void *iter_kernel_bf16(int cpl, int wpw, bool apc, int rg);
+// ... and with the deterministic reduction (IterArgs::det)
+void *iter_kernel_f64_det(int cpl, int wpw, bool apc, int rg);
+void *iter_kernel_f32_det(int cpl, int wpw, bool apc, int rg);
+void *iter_kernel_bf16_det(int cpl, int wpw, bool apc, int rg);
 
 // ---- setup (FP64) -----------------------------------------------------------
 cudaError_t launch_rownorm(const double *A, int64_t lda, int64_t N, int64_t n, double *dinv, int *err,

@@ -6,11 +6,11 @@ namespace apc {
 
 namespace {
 
-void *kernel_for(int precision, int cpl, int wpw, bool apc, int rg) {
+void *kernel_for(int precision, int cpl, int wpw, bool apc, int rg, bool det = false) {
     switch (precision) {
-        case 0: return iter_kernel_f64(cpl, wpw, apc, rg);
-        case 1: return iter_kernel_f32(cpl, wpw, apc, rg);
-        case 2: return iter_kernel_bf16(cpl, wpw, apc, rg);
+        case 0: return det ? iter_kernel_f64_det(cpl, wpw, apc, rg) : iter_kernel_f64(cpl, wpw, apc, rg);
+        case 1: return det ? iter_kernel_f32_det(cpl, wpw, apc, rg) : iter_kernel_f32(cpl, wpw, apc, rg);
+        case 2: return det ? iter_kernel_bf16_det(cpl, wpw, apc, rg) : iter_kernel_bf16(cpl, wpw, apc, rg);
         default: return nullptr;
     }
 }
@@ -63,7 +63,7 @@ int iter_max_clusters(int precision, int cpl, int wpw, int cs, int nw, int rg, s
 }
 
 cudaError_t launch_iter(int precision, int cpl, const IterArgs &a, int clusters, size_t smem, cudaStream_t s) {
-    void *k = kernel_for(precision, cpl, a.wpw, a.mode == MODE_APC, a.rg);
+    void *k = kernel_for(precision, cpl, a.wpw, a.mode == MODE_APC, a.rg, a.det != 0);
     if (!k) return cudaErrorInvalidValue;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (err != cudaSuccess) return err;

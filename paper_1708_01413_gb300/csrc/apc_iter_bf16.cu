@@ -3,6 +3,6 @@
 
 namespace apc {
 void *iter_kernel_bf16(int cpl, int wpw, bool apc, int rg) {
-    return iterk::kernel_for<__nv_bfloat16, float>(cpl, wpw, apc, rg);
+    return iterk::kernel_for<__nv_bfloat16, float, false>(cpl, wpw, apc, rg);
 }
 }  // namespace apc

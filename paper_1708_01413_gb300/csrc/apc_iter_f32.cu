@@ -3,6 +3,6 @@
 
 namespace apc {
 void *iter_kernel_f32(int cpl, int wpw, bool apc, int rg) {
-    return iterk::kernel_for<float, float>(cpl, wpw, apc, rg);
+    return iterk::kernel_for<float, float, false>(cpl, wpw, apc, rg);
 }
 }  // namespace apc

@@ -3,6 +3,6 @@
 
 namespace apc {
 void *iter_kernel_f64(int cpl, int wpw, bool apc, int rg) {
-    return iterk::kernel_for<double, double>(cpl, wpw, apc, rg);
+    return iterk::kernel_for<double, double, false>(cpl, wpw, apc, rg);
 }
 }  // namespace apc

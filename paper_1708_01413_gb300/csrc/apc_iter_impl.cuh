@@ -243,7 +243,7 @@ __device__ __forceinline__ float2 df_from(double v) {
     return make_float2(hi, float(v - double(hi)));
 }
 
-template <typename TQ, typename TS, int CPL, int WPW, bool kAPC, int R>
+template <typename TQ, typename TS, int CPL, int WPW, bool kAPC, int R, bool kDet>
 __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs a) {
     static_assert(R == 1 || R == 2, "one or two rows per group");
     using TC = TS;
@@ -623,31 +623,6 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         return false;
     };
 
-    // Bounded grid-wide barrier (the n-th of this launch waits for n * grid
-    // arrivals); true when the wait ran out of time.
-    uint32_t nbar = 0;
-    auto grid_sync = [&]() -> bool {
-        __syncthreads();
-        if (tid == 0) {
-            __threadfence();
-            red_release_add_u32(a.bar, 1u);
-            const uint32_t target = (nbar + 1) * gridDim.x + a.barrier_skew;
-            if (ld_acquire_u32(a.bar) < target) {
-                const uint64_t t_start = globaltimer_ns();
-                while (ld_acquire_u32(a.bar) < target) {
-                    if (globaltimer_ns() - t_start > a.timeout_ns) {
-                        abort_flag = 1;
-                        abort_code = DEV_TIMEOUT_GRID;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        ++nbar;
-        return __syncthreads_or(abort_flag);
-    };
-
     for (int64_t it = 0; it < a.iters; ++it) {
         cx_cur = cx0;
         for (int t = 0; t < G + 3 && G > 0; ++t)
@@ -655,59 +630,101 @@ __global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs
         gpass += G;
 
         // ---- end of pass: publish z', clear the spare buffer, grid barrier ----
+        if constexpr (kDet) {
+            // deterministic (a separate instantiation): this cluster's partial
+            // z' for its workers; after a grid barrier (every partial visible)
+            // the CTAs sum the partials in cluster order into the z buffer
+            // (each a strided slice), then a second barrier before the next
+            // pass reads it.  Barriers per launch: two per pass.
+            const int64_t tp = a.t0 + it;
+            TS *zp = reinterpret_cast<TS *>(a.zpart) + size_t(cl) * mP + size_t(w0) * P;
+            if (!is_ctl) {
+#pragma unroll
+                for (int sl = 0; sl < WPW; ++sl) {
+                    const int wl = warp * WPW + sl;
+                    if (wl < W_cta) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+#pragma unroll
+                            for (int v = 0; v < V; ++v)
+                                __stcg(zp + size_t(wl) * P + (h * 32 + lane) * V + v, acc[sl][h * V + v]);
+                    }
+                }
+            }
+            cur ^= 1;
+            for (int pass2 = 0; pass2 < 2; ++pass2) {
+                if (pass2 == 1) {
+                    const TS *zpa = reinterpret_cast<const TS *>(a.zpart);
+                    TS *zfull = zbuf + size_t((tp + 1) % 3) * mP;
+                    const int ncl = int(gridDim.x) / cs;
+                    for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP;
+                         i += size_t(gridDim.x) * blockDim.x) {
+                        TS sum = TS(0);
+                        for (int c2 = 0; c2 < ncl; ++c2) sum += __ldcg(zpa + size_t(c2) * mP + i);
+                        zfull[i] = sum;
+                    }
+                    if (it + 1 == a.iters) break;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    red_release_add_u32(a.bar, 1u);
+                    const uint32_t target = uint32_t(2 * it + 1 + pass2) * gridDim.x + a.barrier_skew;
+                    if (ld_acquire_u32(a.bar) < target) {
+                        const uint64_t t_start = globaltimer_ns();
+                        while (ld_acquire_u32(a.bar) < target) {
+                            if (globaltimer_ns() - t_start > a.timeout_ns) {
+                                abort_flag = 1;
+                                abort_code = DEV_TIMEOUT_GRID;
+                                break;
+                            }
+                        }
+                    }
+                    __threadfence();
+                }
+                if (__syncthreads_or(abort_flag)) goto abort_exit;
+            }
+            if (it + 1 < a.iters) load_z(tp + 1);
+            continue;
+        }
         {
             const int64_t tp = a.t0 + it;
+            TS *zout = zbuf + size_t((tp + 1) % 3) * mP + size_t(w0) * P;
+            TS *zsp = zbuf + size_t((tp + 2) % 3) * mP;
+            if (!is_ctl) {
+#pragma unroll
+                for (int sl = 0; sl < WPW; ++sl) {
+                    const int wl = warp * WPW + sl;
+                    if (wl < W_cta) {
+#pragma unroll
+                        for (int h = 0; h < H; ++h)
+                            atomic_add_vec<TS>(zout + size_t(wl) * P + (h * 32 + lane) * V, &acc[sl][h * V], V);
+                    }
+                }
+            }
+            for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x)
+                zsp[i] = TS(0);
             cur ^= 1;
-            if (!a.det) {
-                TS *zout = zbuf + size_t((tp + 1) % 3) * mP + size_t(w0) * P;
-                TS *zsp = zbuf + size_t((tp + 2) % 3) * mP;
-                if (!is_ctl) {
-#pragma unroll
-                    for (int sl = 0; sl < WPW; ++sl) {
-                        const int wl = warp * WPW + sl;
-                        if (wl < W_cta) {
-#pragma unroll
-                            for (int h = 0; h < H; ++h)
-                                atomic_add_vec<TS>(zout + size_t(wl) * P + (h * 32 + lane) * V, &acc[sl][h * V], V);
+            if (it + 1 < a.iters) {
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    red_release_add_u32(a.bar, 1u);
+                    const uint32_t target = uint32_t(it + 1) * gridDim.x + a.barrier_skew;
+                    if (ld_acquire_u32(a.bar) < target) {
+                        const uint64_t t_start = globaltimer_ns();
+                        while (ld_acquire_u32(a.bar) < target) {
+                            if (globaltimer_ns() - t_start > a.timeout_ns) {
+                                abort_flag = 1;
+                                abort_code = DEV_TIMEOUT_GRID;
+                                break;
+                            }
                         }
                     }
+                    __threadfence();
                 }
-                for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x)
-                    zsp[i] = TS(0);
-                if (it + 1 < a.iters) {
-                    if (grid_sync()) goto abort_exit;
-                    load_z(tp + 1);
-                }
-            } else {
-                // deterministic: this cluster's partial z' for its workers, then
-                // (all partials visible) a fixed-order sum over the clusters
-                TS *zp = reinterpret_cast<TS *>(a.zpart) + size_t(cl) * mP + size_t(w0) * P;
-                if (!is_ctl) {
-#pragma unroll
-                    for (int sl = 0; sl < WPW; ++sl) {
-                        const int wl = warp * WPW + sl;
-                        if (wl < W_cta) {
-#pragma unroll
-                            for (int h = 0; h < H; ++h)
-#pragma unroll
-                                for (int v = 0; v < V; ++v)
-                                    __stcg(zp + size_t(wl) * P + (h * 32 + lane) * V + v, acc[sl][h * V + v]);
-                        }
-                    }
-                }
-                if (grid_sync()) goto abort_exit;
-                const TS *zpa = reinterpret_cast<const TS *>(a.zpart);
-                TS *zfull = zbuf + size_t((tp + 1) % 3) * mP;
-                const int ncl = int(gridDim.x) / cs;
-                for (size_t i = size_t(blockIdx.x) * blockDim.x + tid; i < mP; i += size_t(gridDim.x) * blockDim.x) {
-                    TS sum = TS(0);
-                    for (int c2 = 0; c2 < ncl; ++c2) sum += __ldcg(zpa + size_t(c2) * mP + i);
-                    zfull[i] = sum;
-                }
-                if (it + 1 < a.iters) {
-                    if (grid_sync()) goto abort_exit;
-                    load_z(tp + 1);
-                }
+                if (__syncthreads_or(abort_flag)) goto abort_exit;
+                load_z(tp + 1);
             }
         }
     }
@@ -741,10 +758,10 @@ abort_exit:
     cluster_sync_all();
 }
 
-template <typename TQ, typename TS, int RG>
+template <typename TQ, typename TS, int RG, bool DET>
 void *kernel_for_rg(int cpl, int wpw, bool apc) {
-#define APC_K(C, WP) (apc ? reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, true, RG>) \
-                          : reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, false, RG>))
+#define APC_K(C, WP) (apc ? reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, true, RG, DET>) \
+                          : reinterpret_cast<void *>(&apc_iter_kernel<TQ, TS, C, WP, false, RG, DET>))
     if (wpw == 1) {
         switch (cpl) {
             case 2: return APC_K(2, 1);
@@ -762,9 +779,10 @@ void *kernel_for_rg(int cpl, int wpw, bool apc) {
     return nullptr;
 }
 
-template <typename TQ, typename TS>
+template <typename TQ, typename TS, bool DET>
 void *kernel_for(int cpl, int wpw, bool apc, int rg) {
-    return rg == 1 ? kernel_for_rg<TQ, TS, 1>(cpl, wpw, apc) : rg == 2 ? kernel_for_rg<TQ, TS, 2>(cpl, wpw, apc) : nullptr;
+    return rg == 1 ? kernel_for_rg<TQ, TS, 1, DET>(cpl, wpw, apc)
+                   : rg == 2 ? kernel_for_rg<TQ, TS, 2, DET>(cpl, wpw, apc) : nullptr;
 }
 
 }  // namespace iterk
