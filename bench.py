@@ -515,7 +515,7 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
                            "algorithmic_bytes_per_iter": 2 * q_alg}}
 
 
-def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3):
+def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
     """The differentiation workload: A n x n Gaussian, m blocks, k right-hand
     sides, T iterations forward (xbar(T) for all k columns) and the reverse
     sweep back to dL/dB, each one call (apc_forward_rhs / apc_backward_rhs).
@@ -537,13 +537,14 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3):
     offs = inputs.even_offsets(n, m)
     gam, eta = 1.0, 1.5
     out = {"workload": f"Gaussian {n} x {n}, m = {m} blocks of {n // m}, k = {k}, T = {T}"}
-    # the tile tuner on the same single system (one-system batch, k columns)
-    bt = apc.apc_batch_setup([A], [B], [offs])
-    bt.set_params([gam], [eta])
-    bt.reset()
-    tiles, ms_tuned, ms_default = bt.autotune(iters=20, reps=2)
-    out["tuner"] = {"tiles": list(tiles), "ms_per_iter": ms_tuned, "default_256_512_ms_per_iter": ms_default}
-    bt.close()
+    if tune:
+        # the tile tuner on the same single system (one-system batch, k columns)
+        bt = apc.apc_batch_setup([A], [B], [offs])
+        bt.set_params([gam], [eta])
+        bt.reset()
+        tiles, ms_tuned, ms_default = bt.autotune(iters=20, reps=2)
+        out["tuner"] = {"tiles": list(tiles), "ms_per_iter": ms_tuned, "default_256_512_ms_per_iter": ms_default}
+        bt.close()
     for prec in ("bf16", "f32"):
         ctx = apc.apc_setup(A, B[:, 0].contiguous(), offs, precision=prec)
         try:
@@ -757,8 +758,9 @@ def main():
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--batch", type=int, default=1, help="also time the batched solver (256 systems, k = 32)")
     p.add_argument("--rhs", type=int, default=1, help="also time the differentiation workload (k = 16, T = 200)")
-    p.add_argument("--only", default="all", choices=["all", "batch"],
-                   help="batch: time only the batched workload (for profiling)")
+    p.add_argument("--only", default="all", choices=["all", "batch", "rhs"],
+                   help="batch / rhs: time only the batched workload / the differentiation workload (for profiling)")
+    p.add_argument("--rhs-T", type=int, default=200, help="iterations of the differentiation workload")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--batch-iters", type=int, default=50)
     p.add_argument("--no-cpu", action="store_true")
@@ -773,6 +775,12 @@ def main():
         build.build()
         if args.only == "batch":
             run_batch_only(args)
+        elif args.only == "rhs":
+            import torch
+            dev = torch.device("cuda", torch.cuda.current_device())
+            peak, _ = hbm_peak()
+            r = time_rhs(dev, peak, torch.cuda.current_stream(), T=args.rhs_T, reps=args.steps, tune=False)
+            print(json.dumps({"metric": "differentiation workload: forward + reverse sweep", "rhs": r}), flush=True)
         else:
             run_ours(args)
 

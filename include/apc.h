@@ -242,6 +242,20 @@ int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_it
 int apc_backward(apc_ctx *ctx, const double *g_dev, int64_t T, double gamma, double eta, double *db_dev,
                  void *stream);
 
+/* apc_solve_rhs -- apc_solve for k right-hand sides in one call: column j of
+ * B_dev (N x k FP64, row-major, ldb >= k, caller's row order; device) is
+ * solved to the tolerance (or max_iters) exactly as apc_solve solves b, one
+ * column after another (each is the context's right-hand side for its solve;
+ * the b of apc_setup is put back at the end), and its solution goes to column
+ * j of X_dev (n x k FP64, ldx >= k; device).  stats (may be NULL) sums
+ * iterations, checks and seconds over the columns and holds the largest
+ * final relative residual and sweep count.  Errors: as apc_solve
+ * (NOT_CONVERGED if any column missed the tolerance; the others are still
+ * solved), NOMEM. */
+int apc_solve_rhs(apc_ctx *ctx, const double *B_dev, int64_t k, int64_t ldb, double gamma, double eta, double tol,
+                  int64_t max_iters, int64_t check_every, int32_t refine, double *X_dev, int64_t ldx, apc_stats *stats,
+                  void *stream);
+
 /* apc_backward_params -- apc_backward plus the derivatives of L with respect
  * to gamma and eta.  The paper prints no formula for these; they are the
  * reverse-mode derivative of Eq. (cons): with mu_i = lambda_i + (eta/m) lbar at

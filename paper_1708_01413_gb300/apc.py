@@ -31,7 +31,7 @@ EXPORTED = (
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
     "apc_residual_noalloc", "apc_forward_rhs", "apc_backward_rhs", "apc_batch_forward", "apc_batch_backward",
     "apc_monitor", "apc_set_deterministic", "apc_state_bytes", "apc_export_state", "apc_import_state",
-    "apc_batch_set_tiles", "apc_batch_get_tiles", "apc_batch_autotune",
+    "apc_batch_set_tiles", "apc_batch_get_tiles", "apc_batch_autotune", "apc_solve_rhs",
 )
 
 
@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_forward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
     L.apc_monitor.argtypes = [vp, C.POINTER(dbl), vp]
+    L.apc_solve_rhs.argtypes = [vp, vp, i64, i64, dbl, dbl, dbl, i64, i64, i32, vp, i64, C.POINTER(apc_stats), vp]
     L.apc_set_deterministic.argtypes = [vp, i32]
     L.apc_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
     L.apc_export_state.argtypes = [vp, vp, C.c_size_t, vp]
@@ -310,6 +311,26 @@ class Context:
             _check(lib().apc_backward_rhs(self.handle, _ptr(G), k, G.stride(0), int(T), float(gamma), float(eta),
                                           _ptr(out), out.stride(0), _stream(stream)), self.handle)
         return out
+
+    def solve_rhs(self, B, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False, stream=None,
+                  raise_on_error=True):
+        """apc_solve for every column of B (N x k) in one call (apc_solve_rhs);
+        returns (X n x k, stats summed over the columns)."""
+        import torch
+        inf = self.info()
+        B = self._rhs_matrix(B, inf["N"])
+        k = B.shape[1]
+        out = torch.empty((inf["n"], k), dtype=torch.float64, device=self.device)
+        st = apc_stats()
+        with torch.cuda.device(self.device):
+            rc = lib().apc_solve_rhs(self.handle, _ptr(B), k, B.stride(0), float(gamma), float(eta), float(tol),
+                                     int(max_iters), int(check_every), int(bool(refine)), _ptr(out), out.stride(0),
+                                     C.byref(st), _stream(stream))
+        stats = dict(iterations=st.iterations, sweeps=st.sweeps, rel_residual=st.rel_residual, seconds=st.seconds,
+                     residual_checks=st.residual_checks, monitor_checks=st.monitor_checks, rc=rc)
+        if rc != 0 and raise_on_error:
+            _check(rc, self.handle)
+        return out, stats
 
     def solve(self, gamma, eta, tol=1e-10, max_iters=10**6, check_every=100, refine=False,
               out=None, stream=None, raise_on_error=True):

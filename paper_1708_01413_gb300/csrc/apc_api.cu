@@ -661,6 +661,57 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
     return rc;
 }
 
+int apc_solve_rhs(apc_ctx *c, const double *B_dev, int64_t k, int64_t ldb, double gamma, double eta, double tol,
+                  int64_t max_iters, int64_t check_every, int32_t refine, double *X_dev, int64_t ldx, apc_stats *stats,
+                  void *stream) {
+    if (!c || !B_dev || !X_dev || k < 1 || ldb < k || ldx < k)
+        return fail(c, APC_ERR_INVALID_ARG, "apc_solve_rhs: bad pointer, k or leading dimension");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the columns one after another through apc_solve, each as the context's
+    // right-hand side (the stored b is set aside and put back)
+    double *bsave = nullptr, *xcol = nullptr;
+    if (cudaMalloc(&bsave, sizeof(double) * c->N) != cudaSuccess ||
+        cudaMalloc(&xcol, sizeof(double) * c->n) != cudaSuccess) {
+        cudaGetLastError();
+        if (bsave) cudaFree(bsave);
+        return fail(c, APC_ERR_NOMEM, "apc_solve_rhs: staging buffers");
+    }
+    apc_stats total = {};
+    int rc = APC_OK, worst = APC_OK;
+    if (cudaMemcpyAsync(bsave, c->b, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        rc = fail(c, APC_ERR_CUDA, "apc_solve_rhs: copy of b failed");
+    for (int64_t j = 0; rc == APC_OK && j < k; ++j) {
+        cudaError_t e = cudaMemcpy2DAsync(c->rhs, sizeof(double), B_dev + j, sizeof(double) * ldb, sizeof(double), c->N,
+                                          cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && c->d_perm) e = launch_permute_vec(c->rhs, c->d_perm, c->N, 0, c->b, s);
+        else if (e == cudaSuccess) e = cudaMemcpyAsync(c->b, c->rhs, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) { rc = fail(c, APC_ERR_CUDA, "apc_solve_rhs: column copy failed"); break; }
+        apc_stats st = {};
+        const int r = apc_solve(c, gamma, eta, tol, max_iters, check_every, refine, xcol, &st, stream);
+        if (r != APC_OK && r != APC_ERR_NOT_CONVERGED) { rc = r; break; }
+        if (r != APC_OK) worst = r;
+        if (cudaMemcpy2DAsync(X_dev + j, sizeof(double) * ldx, xcol, sizeof(double), sizeof(double), c->n,
+                              cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            rc = fail(c, APC_ERR_CUDA, "apc_solve_rhs: solution copy failed");
+            break;
+        }
+        total.iterations += st.iterations;
+        total.sweeps = std::max(total.sweeps, st.sweeps);
+        total.rel_residual = std::max(total.rel_residual, st.rel_residual);
+        total.seconds += st.seconds;
+        total.residual_checks += st.residual_checks;
+        total.monitor_checks += st.monitor_checks;
+    }
+    const std::string msg = c->last_error;
+    cudaMemcpyAsync(c->b, bsave, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    cudaFree(bsave);
+    cudaFree(xcol);
+    c->last_error = msg;
+    if (stats) *stats = total;
+    return rc != APC_OK ? rc : worst;
+}
+
 int apc_backward(apc_ctx *c, const double *g_dev, int64_t T, double gamma, double eta, double *db_dev,
                  void *stream) {
     if (!c || !g_dev || !db_dev || T < 0) return fail(c, APC_ERR_INVALID_ARG, "bad argument");

@@ -68,3 +68,24 @@ def test_solve_checks_with_the_monitor(prec):
     else:
         assert st["monitor_checks"] > 0
         assert st["residual_checks"] < st["monitor_checks"]
+
+
+def test_solve_rhs_solves_every_column_and_keeps_b():
+    # k right-hand sides through apc_solve_rhs (columns of a wider matrix),
+    # each to 1e-10 with FP32 + refinement; the context's own b is unchanged
+    apc, dev = _env()
+    n, N, m, k = 768, 864, 9, 3
+    A, _, b = inputs.gaussian_system(n, 83, N=N)
+    offs = inputs.even_offsets(N, m)
+    bl = O.partition(A, b, offs)
+    g, e, _ = O.optimal_params(*O.mu_bounds([O.block_qr(Ai)[0] for Ai, _ in bl]))
+    Bw = np.random.default_rng(9).standard_normal((N, k + 2))
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f32")
+    X, st = ctx.solve_rhs(torch.tensor(Bw, device=dev)[:, :k], g, e, tol=1e-10, max_iters=400000, check_every=20,
+                          refine=True)
+    Xh = X.cpu().numpy()
+    for j in range(k):
+        assert O.relative_residual(A, Bw[:, j], Xh[:, j]) <= 1e-10
+    assert st["rel_residual"] <= 1e-10
+    x, _ = ctx.solve(g, e, tol=1e-10, max_iters=400000, check_every=20, refine=True)
+    assert O.relative_residual(A, b, x.cpu().numpy()) <= 1e-10
