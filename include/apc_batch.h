@@ -119,25 +119,30 @@ int apc_batch_backward(apc_batch *b, const double *const *G_dev_host, int64_t T,
  * rows_a rows of every system per sweep-A unit (128 or 256; a unit streams
  * the packed basis of those rows and the machines' iterates), cols_b packed
  * columns per sweep-B unit (128, 256 or 512; a unit streams all rows of those
- * columns), and the sweep-A L2 prefetch distance in windows / machines (0..8).
- * Smaller units give more units to the 152 SMs (a single large system),
- * larger ones fewer unit boundaries (many systems).  Results do not depend on
- * the shape (each row and column is computed by the same arithmetic in the
- * same order).  Default 256 / 512 / 2.  Synchronises the device.
- * apc_batch_get_tiles -- the current shape (any pointer may be NULL).
+ * columns), the sweep-A L2 prefetch distance in windows / machines (0..8),
+ * and the L2 policy of the bulk copies (0 evict-first: operands streamed
+ * once per sweep; 1 normal; 2 evict-last: a basis about the size of L2 may
+ * stay on chip between sweeps).  Smaller units give more units to the 152
+ * SMs (a single large system), larger ones fewer unit boundaries (many
+ * systems).  Results do not depend on these choices (each row and column is
+ * computed by the same arithmetic in the same order).  Default 256 / 512 / 2
+ * / 0.  Synchronises the device.
+ * apc_batch_get_tiles -- the current choices (any pointer may be NULL).
  * Errors: INVALID_ARG, CUDA. */
-int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch);
-int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch);
+int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2);
+int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2);
 
 /* apc_batch_autotune -- the project's tile tuner: times `reps` launches of
- * `iters` iterations (CUDA events on `stream`) for every shape of
- * {256, 128} x {512, 256, 128} x prefetch {2, 0, 1, 4}, keeps the fastest,
- * and returns it with its time per iteration and that of the shape set before
- * the call (ms_default).  Needs apc_batch_set_params and apc_batch_reset
- * first; it advances the iteration state, so apc_batch_reset must follow.
- * Errors: INVALID_ARG, TIMEOUT, CUDA (the previous shape is then restored). */
+ * `iters` iterations (CUDA events on `stream`) for every unit shape of
+ * {256, 128} x {512, 256, 128} x prefetch {2, 0, 1, 4} with the current L2
+ * policy, then the other L2 policies on the fastest shape, keeps the fastest
+ * of all, and returns it with its time per iteration and that of the
+ * choices set before the call (ms_default).  Needs apc_batch_set_params and
+ * apc_batch_reset first; it advances the iteration state, so apc_batch_reset
+ * must follow.  Errors: INVALID_ARG, TIMEOUT, CUDA (the previous choices are
+ * then restored). */
 int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_a, int32_t *cols_b,
-                       int32_t *prefetch, double *ms_best, double *ms_default, void *stream);
+                       int32_t *prefetch, int32_t *l2, double *ms_best, double *ms_default, void *stream);
 
 /* apc_batch_get_xbar -- the master's estimate of system s as FP64,
  * n_s x k row-major with leading dimension ldx >= k, into X_dev.

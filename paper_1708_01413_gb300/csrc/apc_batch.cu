@@ -130,6 +130,7 @@ struct BatchArgs {
     int rowsA;           // rows of a sweep-A unit: 128 or 256
     int colsB;           // columns of a sweep-B unit: 128, 256 or 512
     int prefetch;        // sweep A: L2 prefetch distance in windows / machines (0..8)
+    int l2;              // L2 policy of the bulk copies: 0 evict-first (stream), 1 normal, 2 evict-last
     uint32_t barrier_skew;  // test hook: added to every cross-CTA wait target (0 = normal)
     uint32_t *bar;          // grid barrier after the initialisation (zero at launch)
     int *err;
@@ -202,6 +203,20 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+// L2 cache policy of the bulk copies: evict-first for operands streamed once
+// per sweep (many systems, far more bytes than L2), normal or evict-last so
+// that a single system's basis (about the size of L2) may stay on chip
+// between the two sweeps and across iterations
+__device__ __forceinline__ uint64_t l2_policy(int mode) {
+    uint64_t p;
+    if (mode == 2)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    else if (mode == 1)
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 // pull [src, src + bytes) into L2 ahead of its bulk copy into shared memory
 __device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
@@ -813,7 +828,7 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t *>(tmem_slot);
-    const uint64_t policy = policy_evict_first();
+    const uint64_t policy = l2_policy(a.l2);
     Cursor cur;
     uint32_t uk = 0;   // units handed over so far (same count in every role)
     uint32_t mc = 0;   // sweep-A accumulations (machines) so far (tensor-core warp and consumers)
@@ -1126,6 +1141,7 @@ struct apc_batch {
     int device = 0, k = 1, kp = 16, MT = 1, nsys = 0, grid = 0;
     int units_a = 0, units_b = 0;
     int rowsA = 256, colsB = 512, prefetch = 2;  // unit shape (apc_batch_set_tiles)
+    int l2 = 0;                                  // L2 policy of the bulk copies (apc_batch_set_tiles)
     std::vector<apc_ctx *> ctx;
     std::vector<SysDesc> desc;
     std::vector<int64_t> n;
@@ -1217,6 +1233,7 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s, bool adj = fal
     a.rowsA = b->rowsA;
     a.colsB = b->colsB;
     a.prefetch = b->prefetch;
+    a.l2 = b->l2;
     a.barrier_skew = b->barrier_skew;
     a.bar = reinterpret_cast<uint32_t *>(b->ctr);
     a.err = b->err;
@@ -1576,16 +1593,18 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     return run_graph(b, iters, false, static_cast<cudaStream_t>(stream));
 }
 
-int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch) {
+int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2) {
     if (!b) return bfail(b, APC_ERR_INVALID_ARG, "NULL batch");
     if ((rows_a != kXRows && rows_a != kTileRows) || (cols_b != 128 && cols_b != 256 && cols_b != kColsB) || prefetch < 0 ||
-        prefetch > 8)
-        return bfail(b, APC_ERR_INVALID_ARG, "tiles: rows_a in {128, 256}, cols_b in {128, 256, 512}, prefetch 0..8");
-    if (rows_a == b->rowsA && cols_b == b->colsB && prefetch == b->prefetch) return APC_OK;
+        prefetch > 8 || l2 < 0 || l2 > 2)
+        return bfail(b, APC_ERR_INVALID_ARG,
+                     "tiles: rows_a in {128, 256}, cols_b in {128, 256, 512}, prefetch 0..8, l2 0..2");
+    if (rows_a == b->rowsA && cols_b == b->colsB && prefetch == b->prefetch && l2 == b->l2) return APC_OK;
     BCK(b, cudaDeviceSynchronize());  // no launch may still read the work lists
     b->rowsA = rows_a;
     b->colsB = cols_b;
     b->prefetch = prefetch;
+    b->l2 = l2;
     for (cudaGraphExec_t *g : {&b->graph, &b->graph_adj})
         if (*g) {
             cudaGraphExecDestroy(*g);
@@ -1594,61 +1613,76 @@ int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t pr
     return build_units(b, nullptr);
 }
 
-int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch) {
+int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2) {
     if (!b) return APC_ERR_INVALID_ARG;
     if (rows_a) *rows_a = b->rowsA;
     if (cols_b) *cols_b = b->colsB;
     if (prefetch) *prefetch = b->prefetch;
+    if (l2) *l2 = b->l2;
     return APC_OK;
 }
 
 int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_a, int32_t *cols_b,
-                       int32_t *prefetch, double *ms_best, double *ms_default, void *stream) {
+                       int32_t *prefetch, int32_t *l2, double *ms_best, double *ms_default, void *stream) {
     if (!b || iters < 1 || reps < 1) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
     if (!b->params_set || !b->reset_done)
         return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_set_params and apc_batch_reset must precede the tuning");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {2, 0, 1, 4};
-    const int d_a = b->rowsA, d_b = b->colsB, d_p = b->prefetch;
-    int best_a = d_a, best_b = d_b, best_p = d_p;
+    const int d_a = b->rowsA, d_b = b->colsB, d_p = b->prefetch, d_l = b->l2;
+    int best_a = d_a, best_b = d_b, best_p = d_p, best_l = d_l;
     double best = 1e300, dflt = -1.0;
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
+    // time one shape: ms per iteration, or a negative error code
+    auto time_shape = [&](int ra, int cb, int pf, int l2m, double *per) -> int {
+        int rc = apc_batch_set_tiles(b, ra, cb, pf, l2m);
+        if (rc == APC_OK) rc = run_graph(b, iters, false, s);  // capture and warm-up
+        if (rc != APC_OK) return rc;
+        if (cudaEventRecord(e0, s) != cudaSuccess) return APC_ERR_CUDA;
+        for (int r = 0; r < reps; ++r)
+            if (cudaGraphLaunch(b->graph, s) != cudaSuccess) return APC_ERR_CUDA;
+        if (cudaEventRecord(e1, s) != cudaSuccess) return APC_ERR_CUDA;
+        if ((rc = check_err(b, s)) != APC_OK) return rc;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *per = double(ms) / double(reps * iters);
+        if (ra == d_a && cb == d_b && pf == d_p && l2m == d_l) dflt = *per;
+        if (*per < best) {
+            best = *per;
+            best_a = ra;
+            best_b = cb;
+            best_p = pf;
+            best_l = l2m;
+        }
+        return APC_OK;
+    };
+    // stage 1: unit shapes and prefetch distances with streaming copies;
+    // stage 2: the L2 policies on the best shape
+    const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {2, 0, 1, 4};
     int rc = APC_OK;
+    double per = 0.0;
     for (int ra : cand_a)
         for (int cb : cand_b)
-            for (int pf : cand_p) {
-                if ((rc = apc_batch_set_tiles(b, ra, cb, pf)) != APC_OK) break;
-                if ((rc = run_graph(b, iters, false, s)) != APC_OK) break;  // capture and warm-up
-                if (cudaEventRecord(e0, s) != cudaSuccess) { rc = APC_ERR_CUDA; break; }
-                for (int r = 0; r < reps && rc == APC_OK; ++r)
-                    if (cudaGraphLaunch(b->graph, s) != cudaSuccess) rc = APC_ERR_CUDA;
-                if (rc != APC_OK || cudaEventRecord(e1, s) != cudaSuccess) { rc = APC_ERR_CUDA; break; }
-                if ((rc = check_err(b, s)) != APC_OK) break;
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                const double per = double(ms) / double(reps * iters);
-                if (ra == d_a && cb == d_b && pf == d_p) dflt = per;
-                if (per < best) {
-                    best = per;
-                    best_a = ra;
-                    best_b = cb;
-                    best_p = pf;
-                }
-            }
+            for (int pf : cand_p)
+                if (rc == APC_OK) rc = time_shape(ra, cb, pf, d_l, &per);
+    const int sa = best_a, sb = best_b, sp = best_p;
+    for (int l2m = 0; l2m <= 2 && rc == APC_OK; ++l2m)
+        if (l2m != d_l) rc = time_shape(sa, sb, sp, l2m, &per);
+    if (rc == APC_OK && dflt < 0.0) rc = time_shape(d_a, d_b, d_p, d_l, &per);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != APC_OK) {
         cudaGetLastError();
-        apc_batch_set_tiles(b, d_a, d_b, d_p);
+        apc_batch_set_tiles(b, d_a, d_b, d_p, d_l);
         return rc == APC_ERR_CUDA ? bfail(b, rc, "tuning launch failed") : rc;
     }
-    if ((rc = apc_batch_set_tiles(b, best_a, best_b, best_p)) != APC_OK) return rc;
+    if ((rc = apc_batch_set_tiles(b, best_a, best_b, best_p, best_l)) != APC_OK) return rc;
     b->reset_done = false;  // the tuning advanced the iteration state
     if (rows_a) *rows_a = best_a;
     if (cols_b) *cols_b = best_b;
     if (prefetch) *prefetch = best_p;
+    if (l2) *l2 = best_l;
     if (ms_best) *ms_best = best;
     if (ms_default) *ms_default = dflt;
     return APC_OK;
@@ -1807,7 +1841,7 @@ int multi_rhs_batch(apc_ctx *c, int64_t k, double gamma, double eta, cudaStream_
         }
         c->mrhs_k = int(k);
         // one system: the smallest units give the most units to the SMs
-        const int rc2 = apc_batch_set_tiles(c->mrhs, 128, 128, 2);
+        const int rc2 = apc_batch_set_tiles(c->mrhs, 128, 128, 2, 0);
         if (rc2 != APC_OK) return cfail(c, rc2, "%s", apc_batch_last_error(c->mrhs));
     }
     const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);

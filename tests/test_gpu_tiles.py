@@ -14,7 +14,7 @@ from paper_1708_01413_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-SHAPES = [(256, 512, 2), (128, 512, 2), (256, 128, 0), (128, 256, 4), (128, 128, 1)]
+SHAPES = [(256, 512, 2, 0), (128, 512, 2, 1), (256, 128, 0, 2), (128, 256, 4, 0), (128, 128, 1, 2)]
 
 
 def _env():
@@ -78,7 +78,7 @@ def test_autotune_picks_a_candidate_and_caches_it(tmp_path):
     bt.reset()
     cache = str(tmp_path / "tiles.json")
     tiles, best, dflt = bt.autotune(iters=3, reps=2, cache=cache)
-    assert tiles[0] in (128, 256) and tiles[1] in (128, 256, 512) and tiles[2] in (0, 1, 2, 4)
+    assert tiles[0] in (128, 256) and tiles[1] in (128, 256, 512) and tiles[2] in (0, 1, 2, 4) and tiles[3] in (0, 1, 2)
     assert 0 < best <= dflt
     assert bt.tiles() == tiles
     with pytest.raises(apc.ApcError):  # the tuning advanced the state: reset first
