@@ -588,22 +588,32 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
 }
 
 // ---- sweep B -----------------------------------------------------------------------
+// Rows of Q per sweep-B stage: 32 (eight 4 KB pieces at 512 columns), or 64
+// when the unit is at most 256 columns wide and the xbar' planes of 64 rows
+// (3 x 16 right-hand sides) still fit the slot's 8 KB: a narrow unit then
+// keeps twice the bytes in flight per stage.  Never past the system's rows.
+template <int MT>
+__device__ __forceinline__ int rows_stage_b(int nwin, int npad, int r0) {
+    const int rs = (MT == 1 && nwin <= 4) ? 2 * kRowsStageB : kRowsStageB;
+    return min(rs, npad - r0);
+}
+
 template <int MT>
 __device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, int colsB,
                                  uint64_t policy) {
     const int nwin = min(colsB, d.Cq - col0) / kWin;
-    const uint32_t xbytes = kPlanesB * 16 * MT * 64;  // 32 rows
-    for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
+    constexpr uint32_t prow = kPlanesB * 16 * MT * 2;  // bytes of the xbar' planes per row
+    for (int r0 = 0, rs; r0 < d.npad; r0 += rs) {
+        rs = rows_stage_b<MT>(nwin, d.npad, r0);
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
         const int t = r0 / kTileRows, rr = r0 % kTileRows;
-        mbar_arrive_expect_tx(&R.full[s], uint32_t(nwin) * kRowsStageB * kWin * 2 + xbytes);
+        const uint32_t blk = uint32_t(rs) * kWin * 2;
+        mbar_arrive_expect_tx(&R.full[s], uint32_t(nwin) * blk + uint32_t(rs) * prow);
         for (int j = 0; j < nwin; ++j)
-            tma_load_1d(R.qslot(s) + j * (kRowsStageB * kWin * 2),
-                        d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin,
-                        kRowsStageB * kWin * 2, &R.full[s], policy);
-        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xop + size_t(r0) * (xbytes / kRowsStageB), xbytes, &R.full[s],
-                    policy);
+            tma_load_1d(R.qslot(s) + j * blk, d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin, blk,
+                        &R.full[s], policy);
+        tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xop + size_t(r0) * prow, uint32_t(rs) * prow, &R.full[s], policy);
         ++cur.q;
     }
 }
@@ -669,19 +679,21 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
                             const SysDesc &d, int col0, int colsB, uint32_t tmem) {
     constexpr int NB = kPlanesB * 16 * MT;
     constexpr uint32_t idesc = instr_desc(NB, 1);
-    const int nmt = (min(colsB, d.Cq - col0) + 127) / 128;
+    const int nwin = min(colsB, d.Cq - col0) / kWin;
+    const int nmt = (nwin * kWin + 127) / 128;
     if (ubc > 0 && !R.wait(bfree, (ubc - 1) & 1)) return;
     tc_fence_after();
     bool first = true;
-    for (int r0 = 0; r0 < d.npad; r0 += kRowsStageB) {
+    for (int r0 = 0, rs; r0 < d.npad; r0 += rs) {
+        rs = rows_stage_b<MT>(nwin, d.npad, r0);
+        const uint32_t blk = uint32_t(rs) * kWin * 2;  // one [rs rows][64 columns] piece
         const uint32_t s = cur.q % kQSlots;
         if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
         tc_fence_after();
         const uint32_t sq = smem_u32(R.qslot(s)), sx = sq + kSlotQBytes;
-#pragma unroll
-        for (int ks = 0; ks < kRowsStageB / 16; ++ks) {
+        for (int ks = 0; ks < rs / 16; ++ks) {
             for (int h = 0; h < nmt; ++h)
-                tc_mma(tmem + uint32_t(h * NB), smem_desc(sq + 2 * h * 4096 + ks * 2048, 4096, 1024, 2),
+                tc_mma(tmem + uint32_t(h * NB), smem_desc(sq + 2 * h * blk + ks * 2048, blk, 1024, 2),
                        smem_desc(sx + ks * (NB * 32), 128, 256, 0), idesc, !first);
             first = false;
         }

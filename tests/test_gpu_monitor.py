@@ -79,7 +79,7 @@ def test_solve_rhs_solves_every_column_and_keeps_b():
     offs = inputs.even_offsets(N, m)
     bl = O.partition(A, b, offs)
     g, e, _ = O.optimal_params(*O.mu_bounds([O.block_qr(Ai)[0] for Ai, _ in bl]))
-    Bw = np.random.default_rng(9).standard_normal((N, k + 2))
+    Bw = A @ np.random.default_rng(9).standard_normal((n, k + 2))  # consistent: the system is tall
     ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f32")
     X, st = ctx.solve_rhs(torch.tensor(Bw, device=dev)[:, :k], g, e, tol=1e-10, max_iters=400000, check_every=20,
                           refine=True)
