@@ -504,6 +504,7 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
             "iter_per_s": 1.0 / sec, "ms_per_iter": sec * 1e3, "rhs_iter_per_s": nsys * k / sec,
             "iters_per_launch": iters, "launches": reps, "setup_s": round(setup_s, 3), "grid": info["grid"],
             "tiles": {"rows_a": tiles[0], "cols_b": tiles[1], "prefetch": tiles[2], "l2_policy": tiles[3],
+                      "split_a": tiles[4], "split_b": tiles[5],
                       "tuner_ms_per_iter": ms_tuned, "default_ms_per_iter": ms_default},
             "clocks": clk.summary(),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -116,33 +116,45 @@ int apc_batch_backward(apc_batch *b, const double *const *G_dev_host, int64_t T,
                        void *stream);
 
 /* apc_batch_set_tiles -- the shape of the persistent kernel's work units:
- * rows_a rows of every system per sweep-A unit (128 or 256; a unit streams
- * the packed basis of those rows and the machines' iterates), cols_b packed
- * columns per sweep-B unit (128, 256 or 512; a unit streams all rows of those
- * columns), the sweep-A L2 prefetch distance in windows / machines (0..8),
- * and the L2 policy of the bulk copies (0 evict-first: operands streamed
- * once per sweep; 1 normal; 2 evict-last: a basis about the size of L2 may
- * stay on chip between sweeps).  Smaller units give more units to the 152
- * SMs (a single large system), larger ones fewer unit boundaries (many
- * systems).  Results do not depend on these choices (each row and column is
- * computed by the same arithmetic in the same order).  Default 256 / 512 / 2
- * / 0.  Synchronises the device.
+ *   rows_a   rows of every system per sweep-A unit (128 or 256; a unit
+ *            streams the packed basis of those rows and the machines' iterates);
+ *   cols_b   packed columns per sweep-B unit (128, 256 or 512; a unit streams
+ *            all rows of those columns);
+ *   prefetch the sweep-A L2 prefetch distance in windows / machines (0..8);
+ *   l2       the L2 policy of the bulk copies (0 evict-first: operands
+ *            streamed once per sweep; 1 normal; 2 evict-last);
+ *   split_a, split_b  parts per unit (1, 2, 4 or 8): a sweep-A unit's
+ *            machines, a sweep-B unit's rows are shared out among that many
+ *            CTAs, whose partial row sums / products are added in part order
+ *            by the last part to finish (buffers of split x k x n values per
+ *            system are allocated on first use).
+ * Smaller and split units give more units to the 152 SMs (a single large
+ * system), larger ones fewer unit boundaries (many systems).  For a given
+ * split, results do not depend on the other choices (each row and column is
+ * computed by the same arithmetic in the same order); a split changes the
+ * order of two sums (the machines' row sums, the rows of Q^T xbar'), which
+ * moves results at the level of FP32 rounding.  Default 256 / 512 / 2 / 0 /
+ * 1 / 1.  Synchronises the device.
  * apc_batch_get_tiles -- the current choices (any pointer may be NULL).
- * Errors: INVALID_ARG, CUDA. */
-int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2);
-int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2);
+ * Errors: INVALID_ARG, NOMEM, CUDA. */
+int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2, int32_t split_a,
+                        int32_t split_b);
+int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2,
+                        int32_t *split_a, int32_t *split_b);
 
 /* apc_batch_autotune -- the project's tile tuner: times `reps` launches of
  * `iters` iterations (CUDA events on `stream`) for every unit shape of
- * {256, 128} x {512, 256, 128} x prefetch {2, 0, 1, 4} with the current L2
- * policy, then the other L2 policies on the fastest shape, keeps the fastest
- * of all, and returns it with its time per iteration and that of the
+ * {256, 128} x {512, 256, 128} x prefetch {2, 0, 1, 4} (no split, the current
+ * L2 policy), then the splits {1, 2, 4} x {1, 2, 4} of the fastest shape,
+ * then the other L2 policies on the fastest of those, keeps the fastest of
+ * all, writes it to tiles_out[6] (the arguments of apc_batch_set_tiles in
+ * order; may be NULL) with its time per iteration, and the time of the
  * choices set before the call (ms_default).  Needs apc_batch_set_params and
  * apc_batch_reset first; it advances the iteration state, so apc_batch_reset
- * must follow.  Errors: INVALID_ARG, TIMEOUT, CUDA (the previous choices are
- * then restored). */
-int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_a, int32_t *cols_b,
-                       int32_t *prefetch, int32_t *l2, double *ms_best, double *ms_default, void *stream);
+ * must follow.  Errors: INVALID_ARG, NOMEM, TIMEOUT, CUDA (the previous
+ * choices are then restored). */
+int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *tiles_out, double *ms_best,
+                       double *ms_default, void *stream);
 
 /* apc_batch_get_xbar -- the master's estimate of system s as FP64,
  * n_s x k row-major with leading dimension ldx >= k, into X_dev.

@@ -92,10 +92,9 @@ def lib() -> C.CDLL:
     L.apc_import_state.argtypes = [vp, vp, C.c_size_t, vp]
     L.apc_backward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
     L.apc_batch_forward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
-    L.apc_batch_set_tiles.argtypes = [vp, i32, i32, i32, i32]
-    L.apc_batch_get_tiles.argtypes = [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]
-    L.apc_batch_autotune.argtypes = [vp, i64, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
-                                     C.POINTER(dbl), C.POINTER(dbl), vp]
+    L.apc_batch_set_tiles.argtypes = [vp, i32, i32, i32, i32, i32, i32]
+    L.apc_batch_get_tiles.argtypes = [vp] + [C.POINTER(i32)] * 6
+    L.apc_batch_autotune.argtypes = [vp, i64, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl), vp]
     L.apc_batch_backward.argtypes = [vp, C.POINTER(vp), i64, C.POINTER(vp), vp]
     L.apc_last_error.argtypes = [vp]
     L.apc_last_error.restype = C.c_char_p
@@ -584,29 +583,27 @@ class Batch:
         _check_batch(lib().apc_batch_set_test_hooks(self.handle, int(grid_barrier_skew), float(timeout_s)),
                      self.handle)
 
-    def set_tiles(self, rows_a: int, cols_b: int, prefetch: int, l2: int = 0):
-        """Work-unit shape, prefetch distance and L2 policy of the persistent
-        kernel (apc_batch_set_tiles)."""
-        _check_batch(lib().apc_batch_set_tiles(self.handle, int(rows_a), int(cols_b), int(prefetch), int(l2)),
-                     self.handle)
+    def set_tiles(self, rows_a: int, cols_b: int, prefetch: int, l2: int = 0, split_a: int = 1, split_b: int = 1):
+        """Work-unit shape, prefetch distance, L2 policy and unit splits of the
+        persistent kernel (apc_batch_set_tiles)."""
+        _check_batch(lib().apc_batch_set_tiles(self.handle, int(rows_a), int(cols_b), int(prefetch), int(l2),
+                                               int(split_a), int(split_b)), self.handle)
 
     def tiles(self):
-        ra, cb, pf, l2 = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
-        _check_batch(lib().apc_batch_get_tiles(self.handle, C.byref(ra), C.byref(cb), C.byref(pf), C.byref(l2)),
-                     self.handle)
-        return ra.value, cb.value, pf.value, l2.value
+        v = [C.c_int32() for _ in range(6)]
+        _check_batch(lib().apc_batch_get_tiles(self.handle, *[C.byref(x) for x in v]), self.handle)
+        return tuple(x.value for x in v)
 
     def autotune(self, iters: int = 5, reps: int = 3, cache: str | None = None, stream=None):
         """Run the tile tuner (apc_batch_autotune) and store its choice in the
         tile cache under this batch's key; the iteration state must be reset
         afterwards.  Returns (tiles, ms per iteration tuned, ms default)."""
-        ra, cb, pf, l2 = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        out = (C.c_int32 * 6)()
         best, dflt = C.c_double(), C.c_double()
         with _device(self.device):
-            _check_batch(lib().apc_batch_autotune(self.handle, int(iters), int(reps), C.byref(ra), C.byref(cb),
-                                                  C.byref(pf), C.byref(l2), C.byref(best), C.byref(dflt),
-                                                  _stream(stream)), self.handle)
-        tiles = (ra.value, cb.value, pf.value, l2.value)
+            _check_batch(lib().apc_batch_autotune(self.handle, int(iters), int(reps), out, C.byref(best),
+                                                  C.byref(dflt), _stream(stream)), self.handle)
+        tiles = tuple(int(x) for x in out)
         store_tiles(self.key, tiles, cache)
         return tiles, best.value, dflt.value
 

@@ -53,6 +53,7 @@
 // as the iteration converges, so its error is relative to the step; xbar does
 // not, hence the third plane there.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -95,6 +96,7 @@ constexpr int kBarOffset = kQSlots * kSlotBytes + kXSlots * kXSlotBytes;
 // sweep-A accumulators full/free (two buffers), sweep-B accumulator full/free,
 // drain; then the unit queue (64-bit unit indices) and the tensor-memory address
 constexpr int kNumBars = 2 * kQSlots + 2 * kXSlots + 2 * kUQ + 4 + 3;
+constexpr int kMaxSplit = 8;                       // parts per unit at most (apc_batch_set_tiles)
 constexpr size_t kSmemUsed = size_t(kBarOffset) + kNumBars * sizeof(uint64_t) + kUQ * sizeof(long long) + sizeof(int);
 constexpr size_t kSmemBytes = kSmemUsed + 1024;     // slack to align the slots to 1024 bytes
 constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, sweep B: 4 x 3k
@@ -109,6 +111,10 @@ struct SysDesc {
     const int *coloff;       // [m + 1], multiples of 16
     float2 *Mb;              // [kp][npad]  heavy-ball momentum, double-float; reverse sweep: ell
     float *Gc;               // [kp][Cq]  reverse sweep: dL/dc_i accumulated (FP32)
+    float *Spart;            // [spA][kp][npad] split sweep A: the parts' row sums (or gradients)
+    float *Ypart;            // [spB][kp][Cq]   split sweep B: the parts' products Q^T xbar'
+    int *cntA, *cntB;        // split sweeps: parts done per (row unit, warp) / (column unit, warp, M-tile)
+    int spA, spB, chunkB;    // parts per unit (machines in sweep A, rows in sweep B); rows per sweep-B part
     int npad, m, Cq, C;
     int nuA, nuB;            // units of this system in sweep A and in sweep B
     float g_hi, g_lo, em_hi, em_lo, e1_hi, e1_lo, im_hi, im_lo;
@@ -334,45 +340,108 @@ __device__ __forceinline__ bool acquire_slot(const Ring &R, uint64_t *empty, int
     return R.wait(&empty[q % S], ((q / S) - 1) & 1);
 }
 
+// ---- split units -------------------------------------------------------------------
+// A unit may be split into parts that run on different CTAs: the machines of
+// a sweep-A unit (each part updates its machines' x_i and forms a partial row
+// sum) and the rows of a sweep-B unit (each part a partial product).  Each
+// consumer warp stores its part's values, counts the parts done, and the last
+// one adds all parts in part order (a fixed order) and finishes the unit.
+struct PartA {
+    int i_lo, i_hi;  // machines
+    int c_lo, c_hi;  // their 16-column chunks
+};
+template <bool kSplit>
+__device__ __forceinline__ PartA part_a(const SysDesc &d, int p) {
+    PartA r;
+    if constexpr (kSplit) {
+        const int mc = (d.m + d.spA - 1) / d.spA;
+        r.i_lo = p * mc;
+        r.i_hi = min(d.m, r.i_lo + mc);
+        r.c_lo = __ldg(d.coloff + r.i_lo) >> 4;
+        r.c_hi = __ldg(d.coloff + r.i_hi) >> 4;
+    } else {
+        r.i_lo = 0;
+        r.i_hi = d.m;
+        r.c_lo = 0;
+        r.c_hi = d.C >> 4;
+    }
+    return r;
+}
+template <bool kSplit>
+__device__ __forceinline__ int2 part_b(const SysDesc &d, int p) {  // rows [x, y)
+    if constexpr (kSplit) {
+        const int lo = p * d.chunkB;
+        return make_int2(lo, min(d.npad, lo + d.chunkB));
+    } else {
+        return make_int2(0, d.npad);
+    }
+}
+// Store this part's KP values (part p of np, element q at part + (p KP + q)
+// stride), count the part in *cnt; the warp that completes the count sums
+// the np parts in order into v and resets the count.  True for that warp.
+template <int KP>
+__device__ __forceinline__ bool combine_parts(float (&v)[KP], float *part, size_t stride, int np, int p, int *cnt) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < KP; ++q) __stcg(part + (size_t(p) * KP + q) * stride, v[q]);
+    __threadfence();
+    __syncwarp();
+    int old = 0;
+    if (lane == 0) old = atomicAdd(cnt, 1);
+    old = __shfl_sync(0xffffffffu, old, 0);
+    if (old != np - 1) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < KP; ++q) {
+        float t = 0.0f;
+        for (int pp = 0; pp < np; ++pp) t += __ldcg(part + (size_t(pp) * KP + q) * stride);
+        v[q] = t;
+    }
+    __syncwarp();
+    if (lane == 0) atomicExch(cnt, 0);
+    return true;
+}
+
 // ---- sweep A ---------------------------------------------------------------------
-template <int MT>
-__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, int rowsA, int pf, bool no_x,
-                                 uint64_t policy) {
+template <int MT, bool kSplit>
+__device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, int row0, int part, int rowsA, int pf,
+                                 bool no_x, uint64_t policy) {
     constexpr int KP = 16 * MT;
     // the unit's rows within their 256-row basis tile (the window blocks are
     // [tile rows][64] row-major, so any 128-row part of one is contiguous)
     const int t = row0 / kTileRows, ro = row0 - t * kTileRows;
     const int rows = min(rowsA, d.npad - row0);
-    const int nwin = d.Cq / kWin;
+    const PartA pa = part_a<kSplit>(d, part);
+    const int w_lo = pa.c_lo >> 2, w_hi = (pa.c_hi + 3) >> 2;  // windows holding the part's chunks
     const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = kPlanesA * KP * 128;
     const int u0 = row0 / kXRows, nxb = (rows + kXRows - 1) / kXRows;  // x_i blocks of 128 rows per machine
     const uint32_t xblk = uint32_t(KP) * kXRows * 4;
     auto qsrc = [&](int w) { return d.Q + q_block(d.Cq, d.npad, t, w) + size_t(ro) * kWin; };
-    int pi = 0;  // next machine whose x_i tile is due
+    int pi = pa.i_lo;  // next machine whose x_i tile is due
     // L2 prefetch runs `pf` windows / machines ahead of the shared-memory ring
     // (measured on 256 systems with 256-row units: 2 is 1.5 % faster than 4, 8
     // is 13 % slower, none 4 % slower; an L2 prefetch in sweep B made it 40 %
     // slower); the tile tuner may pick another distance
-    for (int w = 0; w < min(pf, nwin); ++w) prefetch_l2(qsrc(w), qbytes);
+    for (int w = w_lo; w < min(w_lo + pf, w_hi); ++w) prefetch_l2(qsrc(w), qbytes);
     if (!no_x)
-        for (int i = 0; i < min(pf, d.m); ++i)
+        for (int i = pa.i_lo; i < min(pa.i_lo + pf, pa.i_hi); ++i)
             for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, i), xblk);
-    for (int w = 0; w < nwin; ++w) {
+    for (int w = w_lo; w < w_hi; ++w) {
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
         mbar_arrive_expect_tx(&R.full[s], qbytes + zbytes);
         tma_load_1d(R.qslot(s), qsrc(w), qbytes, &R.full[s], policy);
         tma_load_1d(R.qslot(s) + kSlotQBytes, d.Zop + size_t(w) * zbytes, zbytes, &R.full[s], policy);
-        if (w + pf < nwin) prefetch_l2(qsrc(w + pf), qbytes);
+        if (w + pf < w_hi) prefetch_l2(qsrc(w + pf), qbytes);
         ++cur.q;
         // x_i tiles of the machines whose last chunk lies in this window
-        while (!no_x && pi < d.m && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
+        while (!no_x && pi < pa.i_hi && (__ldg(d.coloff + pi + 1) - 16) / kWin == w) {
             const uint32_t xs = cur.x % kXSlots;
             if (!acquire_slot(R, R.xempty, kXSlots, cur.x)) return;
             mbar_arrive_expect_tx(&R.xfull[xs], uint32_t(nxb) * xblk);
             for (int j = 0; j < nxb; ++j)
                 tma_load_1d(R.xslot(xs) + j * xblk, d.X + x_block(d.m, KP, u0 + j, pi), xblk, &R.xfull[xs], policy);
-            if (pi + pf < d.m)
+            if (pi + pf < pa.i_hi)
                 for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, pi + pf), xblk);
             ++cur.x;
             ++pi;
@@ -387,25 +456,28 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
 // matrices).  After the machine's last chunk the buffer is handed to the
 // consumers; a Q slot is released when the instructions reading it are done.
 // Heavy ball: one accumulation over every machine of the tile.
-template <int MT>
+template <int MT, bool kSplit>
 __device__ void sweep_a_mma(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
-                            const SysDesc &d, int row0, int rowsA, bool hb, uint32_t tmem) {
+                            const SysDesc &d, int row0, int part, int rowsA, bool hb, uint32_t tmem) {
     constexpr int NA = kPlanesA * 16 * MT;
     constexpr uint32_t idesc = instr_desc(NA, 0);
     const int rows = min(rowsA, d.npad - row0);
     const int nmt = rows > 128 ? 2 : 1;
-    const int nwin = d.Cq / kWin, nchunk = d.C / 16;
-    int i = 0, iend = __ldg(d.coloff + 1) >> 4;
+    const PartA pa = part_a<kSplit>(d, part);
+    const int w_lo = pa.c_lo >> 2, w_hi = (pa.c_hi + 3) >> 2;
+    int i = pa.i_lo, iend = __ldg(d.coloff + pa.i_lo + 1) >> 4;
     bool first = true;
     uint32_t b = 0;
-    for (int w = 0; w < nwin; ++w) {
+    for (int w = w_lo; w < w_hi; ++w) {
         const uint32_t s = cur.q % kQSlots;
         if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
         tc_fence_after();
         const uint32_t sq = smem_u32(R.qslot(s)), sz = sq + kSlotQBytes;
         for (int kc = 0; kc < 4; ++kc) {
             const int c16 = 4 * w + kc;
-            if (c16 >= nchunk) break;
+            if constexpr (kSplit)
+                if (c16 < pa.c_lo) continue;
+            if (c16 >= pa.c_hi) break;
             if (first) {
                 b = mc & 1;
                 if (mc >= 2 && !R.wait(&dfree[b], ((mc >> 1) - 1) & 1)) return;
@@ -415,11 +487,11 @@ __device__ void sweep_a_mma(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *
                 tc_mma(tmem + uint32_t((2 * b + h) * NA), smem_desc(sq + h * 16384 + kc * 32, 16, 1024, 2),
                        smem_desc(sz + kc * (NA * 32), 128, 256, 0), idesc, !first);
             first = false;
-            if (hb ? c16 + 1 == nchunk : c16 + 1 == iend) {
+            if (hb ? c16 + 1 == pa.c_hi : c16 + 1 == iend) {
                 tc_commit(&dfull[b]);
                 ++mc;
                 first = true;
-                if (!hb && ++i < d.m) iend = __ldg(d.coloff + i + 1) >> 4;
+                if (!hb && ++i < pa.i_hi) iend = __ldg(d.coloff + i + 1) >> 4;
             }
         }
         tc_commit(&R.empty[s]);
@@ -454,10 +526,10 @@ __device__ void store_xop(const SysDesc &d, int64_t row, const float (&xo)[16 * 
 // the master's row update (double-float) and the xbar' planes of sweep B.
 // Reverse sweep (kAdj, one accumulation over every machine, like heavy ball):
 // the step's row update of (ell, lbar) and the planes of the next mu.
-template <int MT, bool kAdj>
+template <int MT, bool kAdj, bool kSplit>
 __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint64_t *dfull, uint64_t *dfree,
-                                 const SysDesc &d, int row0, int rowsA, bool init, bool hb, float gh, float gl,
-                                 uint32_t tmem, bool last) {
+                                 const SysDesc &d, int row0, int part, int rowsA, bool init, bool hb, float gh,
+                                 float gl, uint32_t tmem, bool last) {
     constexpr int KP = 16 * MT, NA = kPlanesA * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int h = warp >> 2, quad = warp & 3;
@@ -479,8 +551,10 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
             xbl[q] = v.y;
         }
     }
-    const int nm = hb ? 1 : d.m;
-    for (int i = 0; i < nm; ++i) {
+    const PartA pa = part_a<kSplit>(d, part);
+    const int nm = hb ? 1 : pa.i_hi - pa.i_lo;
+    for (int ii = 0; ii < nm; ++ii) {
+        const int i = pa.i_lo + ii;
         const uint32_t b = mc & 1;
         if (!R.wait(&dfull[b], (mc >> 1) & 1)) return;
         tc_fence_after();
@@ -528,6 +602,16 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
         }
     }
     if (!wact) return;
+    if constexpr (kSplit) {
+        // a part of a split unit: only the warp that completes the row unit's
+        // parts goes on, with the sum over all parts
+        if (d.spA > 1) {
+            int *cnt = d.cntA + (row0 / rowsA) * kConsumerWarps + (threadIdx.x >> 5);
+            if (!(hb ? combine_parts<KP>(W, d.Spart + grow, size_t(d.npad), d.spA, part, cnt)
+                     : combine_parts<KP>(S, d.Spart + grow, size_t(d.npad), d.spA, part, cnt)))
+                return;
+        }
+    }
     float (&xo)[KP] = S;  // the new xbar (hi part), in place of the row sums
     if constexpr (kAdj) {
         // one step of the reverse sweep through the affine form of App. A.
@@ -598,13 +682,14 @@ __device__ __forceinline__ int rows_stage_b(int nwin, int npad, int r0) {
     return min(rs, npad - r0);
 }
 
-template <int MT>
-__device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, int colsB,
+template <int MT, bool kSplit>
+__device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, int col0, int part, int colsB,
                                  uint64_t policy) {
     const int nwin = min(colsB, d.Cq - col0) / kWin;
+    const int2 pr = part_b<kSplit>(d, part);
     constexpr uint32_t prow = kPlanesB * 16 * MT * 2;  // bytes of the xbar' planes per row
-    for (int r0 = 0, rs; r0 < d.npad; r0 += rs) {
-        rs = rows_stage_b<MT>(nwin, d.npad, r0);
+    for (int r0 = pr.x, rs; r0 < pr.y; r0 += rs) {
+        rs = rows_stage_b<MT>(nwin, pr.y, r0);
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
         const int t = r0 / kTileRows, rr = r0 % kTileRows;
@@ -674,9 +759,9 @@ __device__ void store_v(const SysDesc &d, int col, const float (&Y)[16 * MT], bo
 // MN-major, 128-byte swizzle, 4 KB between blocks; B: the xbar' planes, core
 // matrices), over all row stages; the accumulators go to the consumers once
 // per unit and are reused after they release them.
-template <int MT>
+template <int MT, bool kSplit>
 __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree,
-                            const SysDesc &d, int col0, int colsB, uint32_t tmem) {
+                            const SysDesc &d, int col0, int part, int colsB, uint32_t tmem) {
     constexpr int NB = kPlanesB * 16 * MT;
     constexpr uint32_t idesc = instr_desc(NB, 1);
     const int nwin = min(colsB, d.Cq - col0) / kWin;
@@ -684,8 +769,9 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
     if (ubc > 0 && !R.wait(bfree, (ubc - 1) & 1)) return;
     tc_fence_after();
     bool first = true;
-    for (int r0 = 0, rs; r0 < d.npad; r0 += rs) {
-        rs = rows_stage_b<MT>(nwin, d.npad, r0);
+    const int2 pr = part_b<kSplit>(d, part);
+    for (int r0 = pr.x, rs; r0 < pr.y; r0 += rs) {
+        rs = rows_stage_b<MT>(nwin, pr.y, r0);
         const uint32_t blk = uint32_t(rs) * kWin * 2;  // one [rs rows][64 columns] piece
         const uint32_t s = cur.q % kQSlots;
         if (!R.wait(&R.full[s], (cur.q / kQSlots) & 1)) return;
@@ -708,9 +794,9 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
 // columns 32 (w%4) .. + 31 of each, the tensor-memory lanes of its quarter):
 // Y = the three planes' accumulators summed, then z = Y - c to sweep A
 // (reverse sweep: v = Y, see store_v).
-template <int MT, bool kAdj>
+template <int MT, bool kAdj, bool kSplit>
 __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, uint64_t *bfree, const SysDesc &d,
-                                 int col0, int colsB, uint32_t tmem, bool fin) {
+                                 int col0, int part, int colsB, uint32_t tmem, bool fin) {
     constexpr int KP = 16 * MT, NB = kPlanesB * KP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, quad = warp & 3;
     const int ncols = min(colsB, d.Cq - col0);
@@ -745,6 +831,15 @@ __device__ void sweep_b_consumer(const Ring &R, uint32_t &ubc, uint64_t *bfull, 
         const int h = (warp >> 2) + 2 * hh;
         const int cl = 128 * h + 32 * quad;
         if (cl < ncols) {
+            if constexpr (kSplit) {
+                // a part of a split unit: only the warp that completes the
+                // column unit's parts goes on, with the sum over all parts
+                if (d.spB > 1) {
+                    int *cnt = d.cntB + ((col0 / colsB) * kConsumerWarps + warp) * 2 + hh;
+                    if (!combine_parts<KP>(Y[hh], d.Ypart + col0 + cl + lane, size_t(d.Cq), d.spB, part, cnt))
+                        continue;
+                }
+            }
             if constexpr (kAdj) store_v<MT>(d, col0 + cl + lane, Y[hh], fin);
             else store_z<MT>(d, col0 + cl + lane, Y[hh], false);
         }
@@ -787,7 +882,7 @@ __device__ bool wait_count(const unsigned long long *p, unsigned long long targe
     return false;
 }
 
-template <int MT, bool kAdj>
+template <int MT, bool kAdj, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs a) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ int abort_flag;
@@ -868,7 +963,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
     struct Unit {
         long long it;
         bool is_a, init, hb, edge;  // edge: last step's sweep A / final sweep B of a reverse sweep
-        int2 U;
+        int2 U;                     // (system, first row or column | part << 24)
+        int pos, part;
     };
     auto decode = [&](long long g) {
         Unit u;
@@ -887,6 +983,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
             u.hb = a.hb && !u.init;
             u.edge = false;
         }
+        u.pos = u.U.y & 0xFFFFFF;
+        u.part = u.U.y >> 24;
         return u;
     };
     auto run = [&]() {
@@ -924,8 +1022,10 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 ++uk;
                 if (g < 0) return;
                 const SysDesc &d = a.sys[u.U.x];
-                if (u.is_a) sweep_a_producer<MT>(R, cur, d, u.U.y, a.rowsA, a.prefetch, u.init || u.hb, policy);
-                else sweep_b_producer<MT>(R, cur, d, u.U.y, a.colsB, policy);
+                if (u.is_a)
+                    sweep_a_producer<MT, kSplit>(R, cur, d, u.pos, u.part, a.rowsA, a.prefetch, u.init || u.hb, policy);
+                else
+                    sweep_b_producer<MT, kSplit>(R, cur, d, u.pos, u.part, a.colsB, policy);
             }
         } else if (mma_warp) {
             if (lane != 0) return;
@@ -951,8 +1051,8 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                     tc_fence_after();
                 }
                 prev = u.is_a ? 0 : 1;
-                if (u.is_a) sweep_a_mma<MT>(R, cur, mc, dfull, dfree, d, u.U.y, a.rowsA, u.hb, tmem);
-                else sweep_b_mma<MT>(R, cur, ubc, bfull, bfree, d, u.U.y, a.colsB, tmem);
+                if (u.is_a) sweep_a_mma<MT, kSplit>(R, cur, mc, dfull, dfree, d, u.pos, u.part, a.rowsA, u.hb, tmem);
+                else sweep_b_mma<MT, kSplit>(R, cur, ubc, bfull, bfree, d, u.pos, u.part, a.colsB, tmem);
             }
         } else {
             for (;;) {
@@ -966,10 +1066,11 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
                 const Unit u = decode(g);
                 const SysDesc &d = a.sys[u.U.x];
                 if (u.is_a)
-                    sweep_a_consumer<MT, kAdj>(R, cur, mc, dfull, dfree, d, u.U.y, a.rowsA, u.init, u.hb,
-                                               u.init ? 1.0f : d.g_hi, u.init ? 0.0f : d.g_lo, tmem, u.edge);
+                    sweep_a_consumer<MT, kAdj, kSplit>(R, cur, mc, dfull, dfree, d, u.pos, u.part, a.rowsA, u.init,
+                                                       u.hb, u.init ? 1.0f : d.g_hi, u.init ? 0.0f : d.g_lo, tmem,
+                                                       u.edge);
                 else
-                    sweep_b_consumer<MT, kAdj>(R, ubc, bfull, bfree, d, u.U.y, a.colsB, tmem, u.edge);
+                    sweep_b_consumer<MT, kAdj, kSplit>(R, ubc, bfull, bfree, d, u.pos, u.part, a.colsB, tmem, u.edge);
                 __syncwarp();
                 if (*reinterpret_cast<volatile int *>(&abort_flag)) return;
                 // the unit's global writes are read by other CTAs (bulk
@@ -988,13 +1089,15 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
         if (consumer)
             for (int u = blockIdx.x; u < a.nB; u += gridDim.x) {
                 const int2 U = a.unitsB[u];
+                if ((U.y >> 24) != 0) continue;  // the columns once, not once per part
+                const int col0 = U.y & 0xFFFFFF;
                 const SysDesc &d = a.sys[U.x];
-                const int ncols = min(a.colsB, d.Cq - U.y);
+                const int ncols = min(a.colsB, d.Cq - col0);
                 for (int hh = 0; hh < 2; ++hh) {
                     const int cl = 128 * ((warp >> 2) + 2 * hh) + 32 * (warp & 3);
                     if (cl < ncols) {
                         float Y[16 * MT] = {};
-                        store_z<MT>(d, U.y + cl + lane, Y, true);
+                        store_z<MT>(d, col0 + cl + lane, Y, true);
                     }
                 }
             }
@@ -1154,6 +1257,11 @@ struct apc_batch {
     int units_a = 0, units_b = 0;
     int rowsA = 256, colsB = 512, prefetch = 2;  // unit shape (apc_batch_set_tiles)
     int l2 = 0;                                  // L2 policy of the bulk copies (apc_batch_set_tiles)
+    int splitA = 1, splitB = 1;                  // parts per unit (apc_batch_set_tiles)
+    int split_cap_a = 1, split_cap_b = 1;        // parts the Spart / Ypart buffers hold
+    std::vector<void *> split_bufs;              // Spart / Ypart of every system
+    int *cnt = nullptr;                          // split-part counters of all systems
+    size_t cnt_count = 0;
     std::vector<apc_ctx *> ctx;
     std::vector<SysDesc> desc;
     std::vector<int64_t> n;
@@ -1210,12 +1318,16 @@ int balloc(apc_batch *b, T **p, size_t bytes) {
     return APC_OK;
 }
 
-const void *kernel_ptr(int MT, bool adj) {
+template <int MT>
+const void *kernel_ptr_mt(bool adj, bool split) {
     if (adj)
-        return MT == 1 ? reinterpret_cast<const void *>(&apc_batch_kernel<1, true>)
-                       : reinterpret_cast<const void *>(&apc_batch_kernel<2, true>);
-    return MT == 1 ? reinterpret_cast<const void *>(&apc_batch_kernel<1, false>)
-                   : reinterpret_cast<const void *>(&apc_batch_kernel<2, false>);
+        return split ? reinterpret_cast<const void *>(&apc_batch_kernel<MT, true, true>)
+                     : reinterpret_cast<const void *>(&apc_batch_kernel<MT, true, false>);
+    return split ? reinterpret_cast<const void *>(&apc_batch_kernel<MT, false, true>)
+                 : reinterpret_cast<const void *>(&apc_batch_kernel<MT, false, false>);
+}
+const void *kernel_ptr(int MT, bool adj, bool split) {
+    return MT == 1 ? kernel_ptr_mt<1>(adj, split) : kernel_ptr_mt<2>(adj, split);
 }
 
 // Units sorted by decreasing key, equal keys in insertion order; the CTAs
@@ -1251,18 +1363,10 @@ int launch(apc_batch *b, int init, int64_t iters, cudaStream_t s, bool adj = fal
     a.err = b->err;
     a.timeout_ns = uint64_t(b->timeout_s * 1e9);
     BCK(b, cudaMemsetAsync(b->ctr, 0, sizeof(unsigned long long) * (2 + 2 * size_t(b->nsys)), s));
-    if (adj) {
-        if (b->MT == 1)
-            apc_batch_kernel<1, true><<<b->grid, kThreads, kSmemBytes, s>>>(a);
-        else
-            apc_batch_kernel<2, true><<<b->grid, kThreads, kSmemBytes, s>>>(a);
-    } else {
-        if (b->MT == 1)
-            apc_batch_kernel<1, false><<<b->grid, kThreads, kSmemBytes, s>>>(a);
-        else
-            apc_batch_kernel<2, false><<<b->grid, kThreads, kSmemBytes, s>>>(a);
-    }
-    BCK(b, cudaGetLastError());
+    const bool split = b->splitA > 1 || b->splitB > 1;
+    if (split) BCK(b, cudaMemsetAsync(b->cnt, 0, sizeof(int) * b->cnt_count, s));
+    void *args[] = {&a};
+    BCK(b, cudaLaunchKernel(kernel_ptr(b->MT, adj, split), dim3(b->grid), dim3(kThreads), args, kSmemBytes, s));
     return APC_OK;
 }
 
@@ -1321,11 +1425,19 @@ int build_units(apc_batch *b, cudaStream_t s) {
     std::vector<std::pair<double, int2>> ia, ib;
     for (int sys = 0; sys < b->nsys; ++sys) {
         SysDesc &d = b->desc[sys];
-        d.nuA = (d.npad + b->rowsA - 1) / b->rowsA;
-        d.nuB = (d.Cq + b->colsB - 1) / b->colsB;
+        // parts: machines of a sweep-A unit in groups of ceil(m / splitA);
+        // rows of a sweep-B unit in chunks of a multiple of 64 rows (no part empty)
+        const int mchunk = (d.m + b->splitA - 1) / b->splitA;
+        d.spA = (d.m + mchunk - 1) / mchunk;
+        d.chunkB = ((d.npad + b->splitB - 1) / b->splitB + 63) / 64 * 64;
+        d.spB = (d.npad + d.chunkB - 1) / d.chunkB;
+        d.nuA = (d.npad + b->rowsA - 1) / b->rowsA * d.spA;
+        d.nuB = (d.Cq + b->colsB - 1) / b->colsB * d.spB;
         const double bytes = double(d.npad) * (4.0 * d.Cq + 8.0 * d.m * b->kp);
-        for (int r0 = 0; r0 < d.npad; r0 += b->rowsA) ia.push_back({bytes, make_int2(sys, r0)});
-        for (int c0 = 0; c0 < d.Cq; c0 += b->colsB) ib.push_back({bytes, make_int2(sys, c0)});
+        for (int r0 = 0; r0 < d.npad; r0 += b->rowsA)
+            for (int p = 0; p < d.spA; ++p) ia.push_back({bytes, make_int2(sys, r0 | (p << 24))});
+        for (int c0 = 0; c0 < d.Cq; c0 += b->colsB)
+            for (int p = 0; p < d.spB; ++p) ib.push_back({bytes, make_int2(sys, c0 | (p << 24))});
     }
     const std::vector<int2> ua = by_key_desc(ia), ub = by_key_desc(ib);
     b->units_a = int(ua.size());
@@ -1499,29 +1611,41 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
     // one CTA per SM, all resident at once (the CTAs wait on one another's units)
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-    int per_sm_adj = 0;
-    if (cudaFuncSetAttribute(kernel_ptr(MT, false), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(kernel_ptr(MT, true), cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_ptr(MT, false), kThreads, kSmemBytes) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_adj, kernel_ptr(MT, true), kThreads, kSmemBytes) !=
-            cudaSuccess ||
-        per_sm < 1 || per_sm_adj < 1) {
+    bool resident = true;
+    for (int v = 0; v < 4 && resident; ++v) {
+        const void *k = kernel_ptr(MT, v & 1, v & 2);
+        per_sm = 0;
+        resident = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes)) == cudaSuccess &&
+                   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, kSmemBytes) == cudaSuccess &&
+                   per_sm >= 1;
+    }
+    if (!resident) {
         cudaGetLastError();
         bfail(b, APC_ERR_LAUNCH, "the batched kernel cannot be resident (%zu bytes of shared memory)", kSmemBytes);
         return bail(APC_ERR_LAUNCH);
     }
     b->grid = sms;
-    // work lists, sized for the smallest units (the tile tuner may pick them)
+    // work lists, sized for the smallest units and the most parts (the tile
+    // tuner may pick them), and the split-part counters
     size_t max_a = 0, max_b = 0;
     for (const SysDesc &d : b->desc) {
-        max_a += size_t((d.npad + kXRows - 1) / kXRows);
-        max_b += size_t((d.Cq + 127) / 128);
+        max_a += size_t((d.npad + kXRows - 1) / kXRows) * kMaxSplit;
+        max_b += size_t((d.Cq + 127) / 128) * kMaxSplit;
+        b->cnt_count += size_t((d.npad + kXRows - 1) / kXRows) * kConsumerWarps +
+                        size_t((d.Cq + 127) / 128) * kConsumerWarps * 2;
     }
-    if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * max_a)) || (rc = balloc(b, &b->d_unitsB, sizeof(int2) * max_b)))
+    if ((rc = balloc(b, &b->d_unitsA, sizeof(int2) * max_a)) || (rc = balloc(b, &b->d_unitsB, sizeof(int2) * max_b)) ||
+        (rc = balloc(b, &b->cnt, sizeof(int) * b->cnt_count)))
         return bail(rc);
+    {
+        size_t off = 0;
+        for (SysDesc &d : b->desc) {
+            d.cntA = b->cnt + off;
+            off += size_t((d.npad + kXRows - 1) / kXRows) * kConsumerWarps;
+            d.cntB = b->cnt + off;
+            off += size_t((d.Cq + 127) / 128) * kConsumerWarps * 2;
+        }
+    }
     if ((rc = build_units(b, s)) != APC_OK) return bail(rc);
     cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(SysDesc) * nsys, cudaMemcpyHostToDevice, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1605,18 +1729,52 @@ int apc_batch_iterate(apc_batch *b, int64_t iters, void *stream) {
     return run_graph(b, iters, false, static_cast<cudaStream_t>(stream));
 }
 
-int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2) {
+int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t prefetch, int32_t l2, int32_t split_a,
+                        int32_t split_b) {
     if (!b) return bfail(b, APC_ERR_INVALID_ARG, "NULL batch");
-    if ((rows_a != kXRows && rows_a != kTileRows) || (cols_b != 128 && cols_b != 256 && cols_b != kColsB) || prefetch < 0 ||
-        prefetch > 8 || l2 < 0 || l2 > 2)
+    auto pow2 = [](int v) { return v >= 1 && v <= kMaxSplit && (v & (v - 1)) == 0; };
+    if ((rows_a != kXRows && rows_a != kTileRows) || (cols_b != 128 && cols_b != 256 && cols_b != kColsB) ||
+        prefetch < 0 || prefetch > 8 || l2 < 0 || l2 > 2 || !pow2(split_a) || !pow2(split_b))
         return bfail(b, APC_ERR_INVALID_ARG,
-                     "tiles: rows_a in {128, 256}, cols_b in {128, 256, 512}, prefetch 0..8, l2 0..2");
-    if (rows_a == b->rowsA && cols_b == b->colsB && prefetch == b->prefetch && l2 == b->l2) return APC_OK;
+                     "tiles: rows_a in {128, 256}, cols_b in {128, 256, 512}, prefetch 0..8, l2 0..2, splits 1, 2, 4 "
+                     "or 8");
+    if (rows_a == b->rowsA && cols_b == b->colsB && prefetch == b->prefetch && l2 == b->l2 && split_a == b->splitA &&
+        split_b == b->splitB)
+        return APC_OK;
     BCK(b, cudaDeviceSynchronize());  // no launch may still read the work lists
+    if (split_a > b->split_cap_a || split_b > b->split_cap_b) {
+        // partial sums of the parts: [parts][kp][npad] (sweep A), [parts][kp][Cq] (sweep B)
+        for (void *p : b->split_bufs) cudaFree(p);
+        b->split_bufs.clear();
+        const int ca = std::max(split_a, b->split_cap_a), cb = std::max(split_b, b->split_cap_b);
+        for (SysDesc &d : b->desc) {
+            void *pa = nullptr, *pb = nullptr;
+            if (cudaMalloc(&pa, sizeof(float) * size_t(ca) * b->kp * d.npad) != cudaSuccess ||
+                cudaMalloc(&pb, sizeof(float) * size_t(cb) * b->kp * d.Cq) != cudaSuccess) {
+                cudaGetLastError();
+                if (pa) cudaFree(pa);
+                for (void *p : b->split_bufs) cudaFree(p);
+                b->split_bufs.clear();
+                for (SysDesc &e : b->desc) e.Spart = e.Ypart = nullptr;
+                b->split_cap_a = b->split_cap_b = 1;
+                b->splitA = b->splitB = 1;
+                build_units(b, nullptr);
+                return bfail(b, APC_ERR_NOMEM, "buffers of the split units");
+            }
+            b->split_bufs.push_back(pa);
+            b->split_bufs.push_back(pb);
+            d.Spart = static_cast<float *>(pa);
+            d.Ypart = static_cast<float *>(pb);
+        }
+        b->split_cap_a = ca;
+        b->split_cap_b = cb;
+    }
     b->rowsA = rows_a;
     b->colsB = cols_b;
     b->prefetch = prefetch;
     b->l2 = l2;
+    b->splitA = split_a;
+    b->splitB = split_b;
     for (cudaGraphExec_t *g : {&b->graph, &b->graph_adj})
         if (*g) {
             cudaGraphExecDestroy(*g);
@@ -1625,30 +1783,34 @@ int apc_batch_set_tiles(apc_batch *b, int32_t rows_a, int32_t cols_b, int32_t pr
     return build_units(b, nullptr);
 }
 
-int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2) {
+int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, int32_t *prefetch, int32_t *l2,
+                        int32_t *split_a, int32_t *split_b) {
     if (!b) return APC_ERR_INVALID_ARG;
     if (rows_a) *rows_a = b->rowsA;
     if (cols_b) *cols_b = b->colsB;
     if (prefetch) *prefetch = b->prefetch;
     if (l2) *l2 = b->l2;
+    if (split_a) *split_a = b->splitA;
+    if (split_b) *split_b = b->splitB;
     return APC_OK;
 }
 
-int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_a, int32_t *cols_b,
-                       int32_t *prefetch, int32_t *l2, double *ms_best, double *ms_default, void *stream) {
+int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *tiles_out, double *ms_best,
+                       double *ms_default, void *stream) {
     if (!b || iters < 1 || reps < 1) return bfail(b, APC_ERR_INVALID_ARG, "bad argument");
     if (!b->params_set || !b->reset_done)
         return bfail(b, APC_ERR_INVALID_ARG, "apc_batch_set_params and apc_batch_reset must precede the tuning");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int d_a = b->rowsA, d_b = b->colsB, d_p = b->prefetch, d_l = b->l2;
-    int best_a = d_a, best_b = d_b, best_p = d_p, best_l = d_l;
+    typedef std::array<int, 6> Tiles;  // rows_a, cols_b, prefetch, l2, split_a, split_b
+    const Tiles dflt_t = {b->rowsA, b->colsB, b->prefetch, b->l2, b->splitA, b->splitB};
+    Tiles best_t = dflt_t;
     double best = 1e300, dflt = -1.0;
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
-    // time one shape: ms per iteration, or a negative error code
-    auto time_shape = [&](int ra, int cb, int pf, int l2m, double *per) -> int {
-        int rc = apc_batch_set_tiles(b, ra, cb, pf, l2m);
+    // time one choice: ms per iteration into *per
+    auto time_tiles = [&](const Tiles &t, double *per) -> int {
+        int rc = apc_batch_set_tiles(b, t[0], t[1], t[2], t[3], t[4], t[5]);
         if (rc == APC_OK) rc = run_graph(b, iters, false, s);  // capture and warm-up
         if (rc != APC_OK) return rc;
         if (cudaEventRecord(e0, s) != cudaSuccess) return APC_ERR_CUDA;
@@ -1659,42 +1821,43 @@ int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *rows_
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         *per = double(ms) / double(reps * iters);
-        if (ra == d_a && cb == d_b && pf == d_p && l2m == d_l) dflt = *per;
+        if (t == dflt_t) dflt = *per;
         if (*per < best) {
             best = *per;
-            best_a = ra;
-            best_b = cb;
-            best_p = pf;
-            best_l = l2m;
+            best_t = t;
         }
         return APC_OK;
     };
-    // stage 1: unit shapes and prefetch distances with streaming copies;
-    // stage 2: the L2 policies on the best shape
-    const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {2, 0, 1, 4};
+    // stage 1: unit shapes and prefetch distances (no split, current L2
+    // policy); stage 2: splits of the best shape's units over several CTAs;
+    // stage 3: the L2 policies on the best of those
+    const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {2, 0, 1, 4}, cand_s[] = {1, 2, 4};
     int rc = APC_OK;
     double per = 0.0;
     for (int ra : cand_a)
         for (int cb : cand_b)
             for (int pf : cand_p)
-                if (rc == APC_OK) rc = time_shape(ra, cb, pf, d_l, &per);
-    const int sa = best_a, sb = best_b, sp = best_p;
+                if (rc == APC_OK) rc = time_tiles({ra, cb, pf, dflt_t[3], 1, 1}, &per);
+    const Tiles s1 = best_t;
+    for (int sa : cand_s)
+        for (int sb : cand_s)
+            if (rc == APC_OK && (sa > 1 || sb > 1)) rc = time_tiles({s1[0], s1[1], s1[2], s1[3], sa, sb}, &per);
+    const Tiles s2 = best_t;
     for (int l2m = 0; l2m <= 2 && rc == APC_OK; ++l2m)
-        if (l2m != d_l) rc = time_shape(sa, sb, sp, l2m, &per);
-    if (rc == APC_OK && dflt < 0.0) rc = time_shape(d_a, d_b, d_p, d_l, &per);
+        if (l2m != s2[3]) rc = time_tiles({s2[0], s2[1], s2[2], l2m, s2[4], s2[5]}, &per);
+    if (rc == APC_OK && dflt < 0.0) rc = time_tiles(dflt_t, &per);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != APC_OK) {
         cudaGetLastError();
-        apc_batch_set_tiles(b, d_a, d_b, d_p, d_l);
+        apc_batch_set_tiles(b, dflt_t[0], dflt_t[1], dflt_t[2], dflt_t[3], dflt_t[4], dflt_t[5]);
         return rc == APC_ERR_CUDA ? bfail(b, rc, "tuning launch failed") : rc;
     }
-    if ((rc = apc_batch_set_tiles(b, best_a, best_b, best_p, best_l)) != APC_OK) return rc;
+    if ((rc = apc_batch_set_tiles(b, best_t[0], best_t[1], best_t[2], best_t[3], best_t[4], best_t[5])) != APC_OK)
+        return rc;
     b->reset_done = false;  // the tuning advanced the iteration state
-    if (rows_a) *rows_a = best_a;
-    if (cols_b) *cols_b = best_b;
-    if (prefetch) *prefetch = best_p;
-    if (l2) *l2 = best_l;
+    if (tiles_out)
+        for (int j = 0; j < 6; ++j) tiles_out[j] = best_t[j];
     if (ms_best) *ms_best = best;
     if (ms_default) *ms_default = dflt;
     return APC_OK;
@@ -1852,8 +2015,9 @@ int multi_rhs_batch(apc_ctx *c, int64_t k, double gamma, double eta, cudaStream_
             return cfail(c, rc, "%s", apc_batch_last_error(nullptr));
         }
         c->mrhs_k = int(k);
-        // one system: the smallest units give the most units to the SMs
-        const int rc2 = apc_batch_set_tiles(c->mrhs, 128, 128, 2, 0);
+        // one system: the smallest units, each split over two CTAs, give the
+        // SMs the most work (the tile tuner's choice for an 8192 system, k = 16)
+        const int rc2 = apc_batch_set_tiles(c->mrhs, 128, 128, 1, 0, 2, 2);
         if (rc2 != APC_OK) return cfail(c, rc2, "%s", apc_batch_last_error(c->mrhs));
     }
     const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);
@@ -1947,6 +2111,7 @@ void apc_batch_destroy(apc_batch *b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->graph_adj) cudaGraphExecDestroy(b->graph_adj);
+    for (void *p : b->split_bufs) cudaFree(p);
     for (void *p : b->owned) cudaFree(p);
     for (apc_ctx *c : b->ctx) apc_destroy(c);
     delete b;
