@@ -66,3 +66,20 @@ def test_hb_optimal_params_host_entry_matches_oracle():
     with pytest.raises(apc.ApcError) as ei:
         apc.apc_hb_optimal_params(0.5, 0.2, 4)
     assert ei.value.name == "INVALID_ARG"
+
+
+def test_tile_cache_key_and_store(tmp_path):
+    # the tuner's cache: power-of-two histograms of n and p, k and the SM
+    # count make the key; a stored choice is read back, other keys miss
+    from paper_1708_01413_gb300 import apc
+    k1 = apc.tile_cache_key([300, 310, 4000], [16, 20, 128], 32, 152)
+    assert k1 == apc.tile_cache_key([4000, 310, 300], [128, 16, 20], 32, 152)  # order does not matter
+    assert k1 != apc.tile_cache_key([300, 310, 4000], [16, 20, 128], 16, 152)
+    assert k1 != apc.tile_cache_key([300, 310, 4000], [16, 20, 128], 32, 148)
+    assert k1 != apc.tile_cache_key([300, 600, 4000], [16, 20, 128], 32, 152)
+    path = str(tmp_path / "tiles.json")
+    assert apc.load_tiles(k1, path) is None
+    apc.store_tiles(k1, (128, 256, 1, 2, 2, 4), path)
+    apc.store_tiles("other", (256, 512, 2, 0, 1, 1), path)
+    assert apc.load_tiles(k1, path) == (128, 256, 1, 2, 2, 4)
+    assert apc.load_tiles("missing", path) is None
