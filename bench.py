@@ -583,6 +583,40 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
     return out
 
 
+def summarize(extra):
+    """The headline figures of the comparison legs in a few keys."""
+    out = {}
+
+    def get(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+
+    if "fp32" in extra:
+        out["fp32_iter_per_s"] = get(extra, "fp32", "iter_per_s")
+        out["fp32_hbm_frac"] = get(extra, "fp32", "frac")
+    t = extra.get("tts_n32768", {})
+    for key in ("bf16_ir", "f32_ir"):
+        if key in t:
+            out[f"tts_n32768_{key}_solve_s"] = get(t, key, "seconds")
+            out[f"tts_n32768_{key}_total_s"] = get(t, key, "total_s")
+            out[f"tts_n32768_{key}_rel_residual"] = get(t, key, "rel_residual")
+    if "batch" in extra:
+        out["batch_ms_per_iter"] = get(extra, "batch", "ms_per_iter")
+        out["batch_hbm_frac"] = get(extra, "batch", "roofline", "frac")
+        out["batch_tiles"] = get(extra, "batch", "tiles")
+    if "rhs" in extra:
+        out["rhs_bf16_forward_ms"] = get(extra, "rhs", "bf16", "forward_ms")
+        out["rhs_bf16_backward_ms"] = get(extra, "rhs", "bf16", "backward_ms")
+        out["rhs_bf16_hbm_frac"] = get(extra, "rhs", "bf16", "forward_frac")
+        out["rhs_f32_total_ms"] = get(extra, "rhs", "f32", "total_ms")
+    if "small_f64" in extra:
+        out["small_f64_us_per_iter"] = get(extra, "small_f64", "us_per_iter")
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -720,6 +754,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
         }
         line.update(extra)
+        line["summary"] = summarize(extra)  # last, so that a truncated tail of the line keeps it
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -144,10 +144,10 @@ int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, in
 
 /* apc_batch_autotune -- the project's tile tuner: times `reps` launches of
  * `iters` iterations (CUDA events on `stream`) for every unit shape of
- * {256, 128} x {512, 256, 128} x prefetch {2, 0, 1, 4} (no split, the current
- * L2 policy), then the splits {1, 2, 4} x {1, 2, 4} of the fastest shape,
- * then the other L2 policies on the fastest of those, keeps the fastest of
- * all, writes it to tiles_out[6] (the arguments of apc_batch_set_tiles in
+ * {256, 128} x {512, 256, 128} with every split {1, 2, 4, 8} x {1, 2, 4, 8}
+ * (the current prefetch distance and L2 policy), then the other prefetch
+ * distances {0, 1, 2, 4} and then the other L2 policies on the fastest so
+ * far, keeps the fastest of all, writes it to tiles_out[6] (the arguments of apc_batch_set_tiles in
  * order; may be NULL) with its time per iteration, and the time of the
  * choices set before the call (ms_default).  Needs apc_batch_set_params and
  * apc_batch_reset first; it advances the iteration state, so apc_batch_reset
