@@ -89,3 +89,17 @@ def test_solve_rhs_solves_every_column_and_keeps_b():
     assert st["rel_residual"] <= 1e-10
     x, _ = ctx.solve(g, e, tol=1e-10, max_iters=400000, check_every=20, refine=True)
     assert O.relative_residual(A, b, x.cpu().numpy()) <= 1e-10
+
+
+def test_monitor_needs_a_forward_state():
+    # after a reverse sweep the state holds adjoints: the monitor refuses
+    apc, dev = _env()
+    A, _, b = inputs.gaussian_system(128, 84)
+    offs = inputs.even_offsets(128, 4)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f64")
+    ctx.backward(torch.ones(128, dtype=torch.float64, device=dev), 3, 1.0, 1.5)
+    with pytest.raises(apc.ApcError) as ei:
+        ctx.monitor()
+    assert ei.value.name == "INVALID_ARG"
+    ctx.reset()
+    assert ctx.monitor() == pytest.approx(ctx.residual(ctx.xbar()), rel=1e-8, abs=1e-13)

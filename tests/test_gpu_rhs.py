@@ -145,3 +145,24 @@ def test_differentiation_workload_on_tensor_cores_full_size():
     # norms of its factors, not with its value
     scale = max(float(torch.linalg.norm(JV) * torch.linalg.norm(W)), float(torch.linalg.norm(V) * torch.linalg.norm(JTW)))
     assert abs(lhs - rhs) <= 1e-4 * scale
+
+
+@pytest.mark.parametrize("k", [1, 40])
+def test_rhs_column_loop_on_bf16_context(k):
+    # k = 1 and k > 32 on a BF16 context take the columns one after another
+    # through the iteration kernel (Eq. (cons)), checked against the oracle on
+    # the BF16-rounded bases at the rounding bound
+    apc, dev = _env()
+    n, m, T = 384, 3, 12
+    A, _, _ = inputs.gaussian_system(n, 62)
+    B = np.random.default_rng(13).standard_normal((n, k))
+    offs = inputs.even_offsets(n, m)
+    Qs, Rs = _oracle_system(A, offs)
+    g, e = 1.0, 1.5
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(B[:, 0].copy(), device=dev), offs, precision="bf16")
+    X = ctx.forward_rhs(torch.tensor(B, device=dev), T, g, e).cpu().numpy()
+    Qt = [O.round_bf16(Q) for Q in Qs]
+    for j in (0, k - 1):
+        xs0 = [Q @ O.block_coefficients(Q0, R, B[offs[i]:offs[i + 1], j]) for i, (Q, Q0, R) in enumerate(zip(Qt, Qs, Rs))]
+        ref = O.apc_run(A, B[:, j], offs, g, e, max_iters=T, Qs=Qt, xs0=xs0)
+        assert _rel(X[:, j], ref.xbar) <= 1e-5, j
