@@ -440,7 +440,7 @@ def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
         c32.close()
 
 
-def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None):
+def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None, tiles="tune"):
     """The batched solver (one persistent launch of `iters` iterations per
     step) on the 256-system workload.  Algorithmic bytes per iteration: the
     packed BF16 bases read twice (one product each) and the machines'
@@ -460,7 +460,12 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None)
     info = bt.info()
     bt.set_params([1.0] * nsys, [1.0] * nsys)  # in S for every system; the cost does not depend on them
     bt.reset()
-    tiles, ms_tuned, ms_default = bt.autotune(iters=5, reps=2)  # the project's tile tuner (cached per key)
+    if tiles == "tune":
+        tiles, ms_tuned, ms_default = bt.autotune(iters=5, reps=2)  # the project's tile tuner (cached per key)
+    else:  # given tiles (profiling): rows_a,cols_b,prefetch,l2,split_a,split_b
+        tiles = tuple(int(v) for v in tiles.split(","))
+        bt.set_tiles(*tiles)
+        ms_tuned = ms_default = None
     bt.reset()
     bt.iterate(iters)
     torch.cuda.synchronize()
@@ -766,7 +771,7 @@ def run_batch_only(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     peak, peak_kind = hbm_peak()
     r = time_batch(dev, peak, torch.cuda.current_stream(), iters=args.batch_iters, reps=args.steps,
-                   nsys=args.batch_systems)
+                   nsys=args.batch_systems, tiles=args.batch_tiles)
     r["roofline"]["peak_kind"] = peak_kind
     line = {"metric": "APC iterations/s of the whole batch (all systems, all right-hand sides)",
             "value": r["iter_per_s"], "unit": "iter/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
@@ -799,6 +804,8 @@ def main():
     p.add_argument("--rhs-T", type=int, default=200, help="iterations of the differentiation workload")
     p.add_argument("--batch-systems", type=int, default=256)
     p.add_argument("--batch-iters", type=int, default=50)
+    p.add_argument("--batch-tiles", default="tune",
+                   help="'tune' (the tile tuner) or rows_a,cols_b,prefetch,l2,split_a,split_b (profiling)")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     args = p.parse_args()
