@@ -145,7 +145,9 @@ int apc_batch_get_tiles(const apc_batch *b, int32_t *rows_a, int32_t *cols_b, in
 /* apc_batch_autotune -- the project's tile tuner: times `reps` launches of
  * `iters` iterations (CUDA events on `stream`) for every unit shape of
  * {256, 128} x {512, 256, 128} with every split {1, 2, 4, 8} x {1, 2, 4, 8}
- * (the current prefetch distance and L2 policy), then the other prefetch
+ * (the current prefetch distance and L2 policy; a sweep is split only when
+ * the shape gives it fewer than twice as many units as the grid has CTAs),
+ * then the other prefetch
  * distances {0, 1, 2, 4} and then the other L2 policies on the fastest so
  * far, keeps the fastest of all, writes it to tiles_out[6] (the arguments of apc_batch_set_tiles in
  * order; may be NULL) with its time per iteration, and the time of the

@@ -1834,11 +1834,26 @@ int apc_batch_autotune(apc_batch *b, int64_t iters, int32_t reps, int32_t *tiles
     const int cand_a[] = {256, 128}, cand_b[] = {512, 256, 128}, cand_p[] = {0, 1, 2, 4}, cand_s[] = {1, 2, 4, 8};
     int rc = APC_OK;
     double per = 0.0;
+    // splits only pay when a shape leaves SMs without units: a sweep's units
+    // are multiplied by its split only while the unsplit count is below twice
+    // the grid (many systems already give every SM several units)
+    auto units = [&](int ra, int cb, int *na, int *nb) {
+        *na = *nb = 0;
+        for (const SysDesc &d : b->desc) {
+            *na += (d.npad + ra - 1) / ra;
+            *nb += (d.Cq + cb - 1) / cb;
+        }
+    };
     for (int ra : cand_a)
-        for (int cb : cand_b)
+        for (int cb : cand_b) {
+            int na = 0, nb = 0;
+            units(ra, cb, &na, &nb);
             for (int sa : cand_s)
-                for (int sb : cand_s)
+                for (int sb : cand_s) {
+                    if ((sa > 1 && na >= 2 * b->grid) || (sb > 1 && nb >= 2 * b->grid)) continue;
                     if (rc == APC_OK) rc = time_tiles({ra, cb, dflt_t[2], dflt_t[3], sa, sb}, &per);
+                }
+        }
     const Tiles s1 = best_t;
     for (int pf : cand_p)
         if (rc == APC_OK && pf != s1[2]) rc = time_tiles({s1[0], s1[1], pf, s1[3], s1[4], s1[5]}, &per);
