@@ -77,7 +77,9 @@ typedef struct apc_stats {
  * Sec. 2 (partition) and Sec. 3.3 (QR).  For block i (rows
  * row_offsets_host[i] .. row_offsets_host[i+1]-1) the rows are scaled to unit
  * length (this leaves P_i unchanged) and A_i^T = Q_i R_i is computed by
- * two passes of Cholesky QR in FP64.  Q_i is then stored in the precision of
+ * Cholesky QR in FP64: two passes, or one for an FP32 / BF16 context whose
+ * first pass is already orthonormal far below the stored rounding (see
+ * apc_setup_report).  Q_i is then stored in the precision of
  * opt->precision.  A copy of A and b (FP64) is kept for FP64 residuals.
  *   A_dev  : N x n, row-major, leading dimension lda >= n, FP64, device.
  *   b_dev  : N, FP64, device.
@@ -343,6 +345,14 @@ int apc_import_state(apc_ctx *ctx, const void *host_buf, size_t bytes, void *str
  * returns cleanly and apc_iterate reports APC_ERR_TIMEOUT; the context stays
  * usable (apc_reset, then iterate).  Errors: INVALID_ARG. */
 int apc_set_test_hooks(apc_ctx *ctx, int32_t grid_barrier_skew, double timeout_s);
+
+/* apc_setup_report -- how the blocks were factored: the number of Cholesky-QR
+ * passes (2 for FP64 contexts; 1 for FP32 / BF16 contexts when the first
+ * pass's basis was probed orthonormal to below 1e-11 / 1e-8, far under the
+ * rounding of the stored basis, else 2) and that probe's largest value over
+ * the blocks, ||Q_i^T Q_i v - v|| / ||v|| for a fixed +-1 vector v (-1 when not
+ * probed).  Either pointer may be NULL.  Errors: INVALID_ARG. */
+int apc_setup_report(const apc_ctx *ctx, int32_t *qr_passes, double *orth_probe);
 
 /* apc_context_info -- sizes chosen at setup: padded block width, cluster
  * size, number of clusters, bytes of Q and rows of Q per pipeline step.  Any

@@ -31,7 +31,7 @@ EXPORTED = (
     "apc_batch_get_x", "apc_batch_set_test_hooks", "apc_batch_info", "apc_batch_last_error", "apc_batch_destroy",
     "apc_residual_noalloc", "apc_forward_rhs", "apc_backward_rhs", "apc_batch_forward", "apc_batch_backward",
     "apc_monitor", "apc_set_deterministic", "apc_state_bytes", "apc_export_state", "apc_import_state",
-    "apc_batch_set_tiles", "apc_batch_get_tiles", "apc_batch_autotune", "apc_solve_rhs",
+    "apc_batch_set_tiles", "apc_batch_get_tiles", "apc_batch_autotune", "apc_solve_rhs", "apc_setup_report",
 )
 
 
@@ -85,6 +85,7 @@ def lib() -> C.CDLL:
     L.apc_residual_noalloc.argtypes = [vp, i64, i64, i64, vp, vp, vp, C.POINTER(dbl), vp]
     L.apc_forward_rhs.argtypes = [vp, vp, i64, i64, i64, dbl, dbl, vp, i64, vp]
     L.apc_monitor.argtypes = [vp, C.POINTER(dbl), vp]
+    L.apc_setup_report.argtypes = [vp, C.POINTER(i32), C.POINTER(dbl)]
     L.apc_solve_rhs.argtypes = [vp, vp, i64, i64, dbl, dbl, dbl, i64, i64, i32, vp, i64, C.POINTER(apc_stats), vp]
     L.apc_set_deterministic.argtypes = [vp, i32]
     L.apc_state_bytes.argtypes = [vp, C.POINTER(C.c_size_t)]
@@ -179,6 +180,13 @@ class Context:
                                       C.byref(cs), C.byref(cl), C.byref(cb), C.byref(rg)), self.handle)
         return dict(n=n.value, N=N.value, m=m.value, width=w.value, cluster_size=cs.value,
                     clusters=cl.value, q_bytes=cb.value, rows_per_group=rg.value)
+
+    def setup_report(self) -> dict:
+        """Cholesky-QR passes taken at set-up and the first pass's probed
+        departure from orthogonality (apc_setup_report)."""
+        n, e = C.c_int32(), C.c_double()
+        _check(lib().apc_setup_report(self.handle, C.byref(n), C.byref(e)), self.handle)
+        return {"qr_passes": n.value, "orth_probe": e.value}
 
     def reset(self, rhs=None, stream=None):
         _check(lib().apc_reset(self.handle, _ptr(rhs), _stream(stream)), self.handle)

@@ -15,6 +15,16 @@
 
 using namespace apc;
 
+namespace apc {
+// Departure from orthogonality of each block's basis from a Cholesky-QR pass
+// (QT: [m][P][n] FP64, Q_b = QT_b^T) along a fixed +-1 vector: err[b] =
+// ||Q_b^T Q_b v - v|| / ||v||.  Y: m x n FP64 scratch (apc_setup.cu).
+cudaError_t launch_orth_probe(const double *QT, const int32_t *p_dev, int m, int P, int64_t n, double *Y, double *err,
+                              cudaStream_t s);
+// R_b = I for every block ([m][P][P], zero padding).
+cudaError_t launch_identity(double *R, const int32_t *p_dev, int m, int P, cudaStream_t s);
+}  // namespace apc
+
 
 namespace {
 
@@ -426,14 +436,39 @@ int apc_setup(apc_ctx **out, const double *A_dev, int64_t N, int64_t n, int64_t 
     CKB2(launch_chol(G, c->Rinv1, c->d_p, m, int(P), 1e-14, c->err + 2, s));
     CKB2(cudaMemcpyAsync(c->R1, G, sizeof(double) * m * P * P, cudaMemcpyDeviceToDevice, s));
     CKB2(launch_qt(c->A, n, c->d_rowstart, c->d_p, c->dinv, c->Rinv1, m, int(P), n, QT1, s));
-    CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
-    CKB2(launch_gram(QT1, n, rs2, c->d_p, nullptr, m, int(P), n, G, s));
-    CKB2(launch_chol(G, c->Rinv2, c->d_p, m, int(P), 1e-14, c->err + 3, s));
-    CKB2(cudaMemcpyAsync(c->R2, G, sizeof(double) * m * P * P, cudaMemcpyDeviceToDevice, s));
-    CKB2(launch_qt(QT1, n, rs2, c->d_p, nullptr, c->Rinv2, m, int(P), n, QT2, s));
+    // The second pass restores orthogonality lost to rounding in the first
+    // (about u kappa(A_i)^2).  FP64 contexts always take it.  FP32 and BF16
+    // contexts store Q rounded to 2^-24 or 2^-9, so a first pass whose basis
+    // is orthonormal to far below that is kept: a probe measures
+    // ||Q_i^T Q_i v - v|| / ||v|| for every block (two reads of the basis,
+    // against p_i + 1 for a second pass) and the pass is left out when the
+    // largest is below 1e-11 (FP32) or 1e-8 (BF16).
+    bool second_pass = true;
+    c->orth_probe = -1.0;
+    if (precision != APC_F64) {
+        CKB2(launch_orth_probe(QT1, c->d_p, m, int(P), n, QT2, G, s));
+        std::vector<double> perr(m);
+        CKB2(cudaMemcpyAsync(perr.data(), G, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+        CKB2(cudaStreamSynchronize(s));
+        double worst = 0.0;
+        for (double e : perr) worst = std::isfinite(e) ? std::max(worst, e) : 1e300;
+        c->orth_probe = worst;
+        second_pass = !(worst <= (precision == APC_F32 ? 1e-11 : 1e-8));
+    }
+    if (second_pass) {
+        CKB2(cudaMemsetAsync(G, 0, sizeof(double) * m * P * P, s));
+        CKB2(launch_gram(QT1, n, rs2, c->d_p, nullptr, m, int(P), n, G, s));
+        CKB2(launch_chol(G, c->Rinv2, c->d_p, m, int(P), 1e-14, c->err + 3, s));
+        CKB2(cudaMemcpyAsync(c->R2, G, sizeof(double) * m * P * P, cudaMemcpyDeviceToDevice, s));
+        CKB2(launch_qt(QT1, n, rs2, c->d_p, nullptr, c->Rinv2, m, int(P), n, QT2, s));
+    } else {
+        CKB2(launch_identity(c->Rinv2, c->d_p, m, int(P), s));
+        CKB2(launch_identity(c->R2, c->d_p, m, int(P), s));
+    }
+    c->qr_passes = second_pass ? 2 : 1;
     c->q_bytes = size_t(n) * m * P * q_elem_size(precision);
     if (dalloc(c, &c->Q, c->q_bytes)) return bail2(APC_ERR_NOMEM);
-    CKB2(launch_pack(QT2, m, int(P), n, precision, c->Q, s));
+    CKB2(launch_pack(second_pass ? QT2 : QT1, m, int(P), n, precision, c->Q, s));
     CKB2(cudaMemcpyAsync(herr, c->err, sizeof(herr), cudaMemcpyDeviceToHost, s));
     CKB2(cudaStreamSynchronize(s));
     free_scratch();
@@ -937,6 +972,13 @@ int apc_set_test_hooks(apc_ctx *c, int32_t grid_barrier_skew, double timeout_s) 
     if (!c || grid_barrier_skew < 0 || !(timeout_s > 0.0)) return fail(c, APC_ERR_INVALID_ARG, "bad argument");
     c->test_barrier_skew = uint32_t(grid_barrier_skew);
     c->timeout_s = timeout_s;
+    return APC_OK;
+}
+
+int apc_setup_report(const apc_ctx *c, int32_t *qr_passes, double *orth_probe) {
+    if (!c) return APC_ERR_INVALID_ARG;
+    if (qr_passes) *qr_passes = c->qr_passes;
+    if (orth_probe) *orth_probe = c->orth_probe;
     return APC_OK;
 }
 

@@ -29,6 +29,8 @@ struct apc_ctx {
     double timeout_s = 2.0;
     uint32_t test_barrier_skew = 0;
     size_t q_bytes = 0;
+    int qr_passes = 2;          // Cholesky-QR passes taken at set-up (1 or 2)
+    double orth_probe = -1.0;   // the first pass's probed departure from orthogonality (-1: not probed)
     void *zpart = nullptr;      // deterministic reduction: per-cluster partial z' [clusters][m][P]
     int det = 0;
     int64_t *d_perm = nullptr;  // apc_setup_rows: row k of the blocked system is row d_perm[k] of the caller's

@@ -272,6 +272,57 @@ __global__ void bsolve_kernel(const TS *z, const int64_t *row_start, const int32
     }
 }
 
+// ---- orthogonality probe of a first Cholesky-QR pass ----------------------------
+// With v the +-1 vector v_c = sign pattern of a hash of c (c < p), Y_b = Q_b v
+// (Q_b = QT_b^T, n x p) and u_b = Q_b^T Y_b; ||u_b - v|| / ||v|| is the
+// departure of Q_b^T Q_b from the identity along v.
+__device__ __forceinline__ double probe_sign(int c) { return ((uint32_t(c) * 0x9E3779B1u) >> 31) ? 1.0 : -1.0; }
+
+__global__ void probe_y_kernel(const double *QT, const int32_t *pcount, int P, int64_t n, double *Y) {
+    const int b = blockIdx.y;
+    const int p = pcount[b];
+    const double *Qb = QT + size_t(b) * P * n;
+    for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += int64_t(gridDim.x) * blockDim.x) {
+        double y = 0.0;
+        for (int c = 0; c < p; ++c) y = fma(probe_sign(c), Qb[size_t(c) * n + j], y);
+        Y[size_t(b) * n + j] = y;
+    }
+}
+
+// err[b] = ||Q_b^T Y_b - v|| / ||v||, one CTA per block, one warp per row c
+__global__ void probe_u_kernel(const double *QT, const double *Y, const int32_t *pcount, int P, int64_t n,
+                               double *err) {
+    __shared__ double part[32];
+    const int b = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int p = pcount[b];
+    const double *Qb = QT + size_t(b) * P * n, *Yb = Y + size_t(b) * n;
+    double acc = 0.0;
+    for (int c = warp; c < p; c += nw) {
+        double u = 0.0;
+        for (int64_t j = lane; j < n; j += 32) u = fma(Qb[size_t(c) * n + j], Yb[j], u);
+        for (int off = 16; off; off >>= 1) u += __shfl_xor_sync(0xffffffffu, u, off);
+        const double d = u - probe_sign(c);
+        acc = fma(d, d, acc);
+    }
+    if (lane == 0) part[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += part[w];
+        err[b] = sqrt(t / double(p > 0 ? p : 1));
+    }
+}
+
+// R_b = I (p x p, zero padding): the second Cholesky-QR pass left out
+__global__ void identity_kernel(double *R, const int32_t *pcount, int P) {
+    const int b = blockIdx.x;
+    const int p = pcount[b];
+    for (int64_t idx = threadIdx.x; idx < int64_t(P) * P; idx += blockDim.x) {
+        const int i = int(idx / P), j = int(idx % P);
+        R[size_t(b) * P * P + idx] = (i == j && i < p) ? 1.0 : 0.0;
+    }
+}
+
 // ---- free residual monitor -------------------------------------------------------
 // Row block b of the residual of xbar: A_b xbar - rhs_b = D^{-1} R'^T (Q_b^T xbar - c_b)
 // with (D A_b)^T = Q_b R', R' = R2 R1 the two Cholesky factors, and
@@ -533,6 +584,19 @@ cudaError_t launch_bsolve(const void *z, const int64_t *row_start_dev, const int
     else
         bsolve_kernel<float><<<unsigned(m), 256, sh, s>>>(static_cast<const float *>(z), row_start_dev, p_dev,
                                                          dinv, Rinv1, Rinv2, P, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orth_probe(const double *QT, const int32_t *p_dev, int m, int P, int64_t n, double *Y, double *err,
+                              cudaStream_t s) {
+    probe_y_kernel<<<dim3(unsigned(std::min<int64_t>((n + 255) / 256, 256)), unsigned(m)), 256, 0, s>>>(QT, p_dev, P, n,
+                                                                                                     Y);
+    probe_u_kernel<<<unsigned(m), 256, 0, s>>>(QT, Y, p_dev, P, n, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_identity(double *R, const int32_t *p_dev, int m, int P, cudaStream_t s) {
+    identity_kernel<<<unsigned(m), 256, 0, s>>>(R, p_dev, P);
     return cudaGetLastError();
 }
 

@@ -646,3 +646,35 @@ def test_full_size_workloads_match_stored_basis_oracle(name, n, m, prec):
         dx = xs1[i] - xs0[i]
         ratio = float(torch.linalg.norm(Ai @ dx) / (torch.linalg.norm(Ai) * torch.linalg.norm(dx)))
         assert ratio <= tol, (name, int(i), ratio)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+def test_setup_passes_and_orthogonality(prec):
+    # FP64 contexts take both Cholesky-QR passes; FP32 / BF16 contexts keep a
+    # first pass that the probe finds orthonormal far below their rounding,
+    # and the stored basis is still orthonormal and spans the blocks' rows;
+    # an ill-conditioned block (rows nearly dependent) makes the probe fail
+    # and the second pass run
+    apc, dev = _apc(), _dev()
+    n, m = 600, 4
+    A, _, b = inputs.gaussian_system(n, 71)
+    offs = inputs.even_offsets(n, m)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    rep = ctx.setup_report()
+    if prec == "f64":
+        assert rep["qr_passes"] == 2 and rep["orth_probe"] == -1.0
+    else:
+        assert rep["qr_passes"] == 1 and 0.0 <= rep["orth_probe"] <= 1e-11
+    tol = {"f64": 1e-12, "f32": 1e-6, "bf16": 1e-2}[prec]
+    for i, (Ai, _) in enumerate(O.partition(A, b, offs)):
+        Q = ctx.basis(i).cpu().numpy()
+        assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() <= 4 * tol
+        assert np.abs(np.eye(n) - Q @ Q.T - O.projector(Ai)).max() <= 4 * tol
+    # nearly dependent rows: kappa(A_1) ~ 1e6, the first pass loses orthogonality
+    A2 = A.copy()
+    A2[1] = A2[0] + 1e-6 * A2[1]
+    c2 = apc.apc_setup(torch.tensor(A2, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    if prec != "f64":
+        assert c2.setup_report()["qr_passes"] == 2
+    Q = c2.basis(0).cpu().numpy()
+    assert np.abs(Q.T @ Q - np.eye(Q.shape[1])).max() <= 4 * tol
