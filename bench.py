@@ -597,7 +597,7 @@ def summarize(extra):
             if not isinstance(d, dict) or k not in d:
                 return None
             d = d[k]
-        return round(d, 4) if isinstance(d, float) else d
+        return float(f"{d:.4g}") if isinstance(d, float) else d
 
     if "fp32" in extra:
         out["fp32_iter_per_s"] = get(extra, "fp32", "iter_per_s")
