@@ -23,6 +23,9 @@ Also on the same JSON line:
   tts_n32768   the same comparison at the headline size on a tall Gaussian
                system (36864 x 32768, 144 blocks of 256, kappa(X) ~ 1e3), with
                the spectrum estimated on the GPU (Lanczos);
+  tts_dc<c>    the same on the headline's matrix family made tall (36864 x
+               32768, D_r over 4 decades, D_c narrowed to 10^-c..10^c): the
+               square matrix has kappa(X) >= 1e6 even at D_c = I;
   batch        the batched solver on 256 independent systems (n ~ U{256..4096},
                A = G + 0.5 sqrt(n) I, blocks p_i ~ U{16..128}, k = 32
                right-hand sides, BF16 bases): iterations per second of the
@@ -319,24 +322,36 @@ def time_to_tolerance(dev, tol=1e-10):
     return out
 
 
-def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
+def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256, col_decades=None, max_iters=5000,
+                            plain=True, lanczos_steps=150, lo_margin=0.98):
     """Time to relative residual `tol` at the headline size: a tall Gaussian
     system (N = 36864 equations, n = 32768 unknowns, 144 blocks of 256; kappa(X)
     stays ~1e3 at any size for this aspect ratio), BF16 + FP64 refinement
     against FP32 + FP64 refinement, plus the residual plain FP32 reaches in a
-    bounded run.  Each context estimates the extreme eigenvalues of its own X
-    with the GPU Lanczos (apc_spectral_bounds), margins 0.98 / 1.01, then
-    Theorem 1's (gamma, eta).  `seconds` covers the solve alone; set-up and
-    Lanczos are reported beside it, and `total_s` is the user-visible time to
-    the tolerance: set-up + Lanczos + solve.  FP32 checks its inner solves with
-    the free residual monitor, BF16 with FP64 residuals (counts beside)."""
+    bounded run.  With `col_decades` = c the matrix is the headline's family
+    instead, tall: A = D_r G D_c, D_r log-uniform in [1e-2, 1e2], D_c narrowed to
+    [10^-c, 10^c] (the square matrix has kappa(X) >= 1e6 even at D_c = I).
+    Each context estimates the extreme eigenvalues of its own X with the GPU
+    Lanczos (apc_spectral_bounds), margins 0.98 / 1.01, then Theorem 1's
+    (gamma, eta).  `seconds` covers the solve alone; set-up and Lanczos are
+    reported beside it, and `total_s` is the user-visible time to the
+    tolerance: set-up + Lanczos + solve.  FP32 checks its inner solves with the
+    free residual monitor, BF16 with FP64 residuals (counts beside)."""
     import torch
     from paper_1708_01413_gb300 import apc, inputs
     m = N // p
-    A, x_true, b = inputs.gaussian_system_torch(n, 13, dev, N=N)
+    if col_decades is None:
+        A, x_true, b = inputs.gaussian_system_torch(n, 13, dev, N=N)
+        workload = f"tall Gaussian N={N}, n={n}, m={m} blocks of {p}"
+    else:
+        A, x_true, b = inputs.scaled_system_torch(n, 17, dev, N=N, col_decades=col_decades)
+        workload = (f"tall A=D_r G D_c N={N}, n={n}, D_r log-uniform 1e-2..1e2, D_c log-uniform "
+                    f"1e-{col_decades:g}..1e{col_decades:g}, m={m} blocks of {p}")
     offs = inputs.even_offsets(N, m)
-    out = {"workload": f"tall Gaussian N={N}, n={n}, m={m} blocks of {p}", "tol": tol}
-    runs = (("bf16_ir", "bf16", True, 5000), ("f32_ir", "f32", True, 5000), ("f32_plain", "f32", False, 2000))
+    out = {"workload": workload, "tol": tol}
+    runs = [("bf16_ir", "bf16", True, max_iters), ("f32_ir", "f32", True, max_iters)]
+    if plain:
+        runs.append(("f32_plain", "f32", False, 2000))
     for key, prec, refine, max_iters in runs:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -345,9 +360,9 @@ def time_to_tolerance_large(dev, tol=1e-10, n=32768, N=36864, p=256):
         t_setup = time.perf_counter() - t0
         try:
             t0 = time.perf_counter()
-            lo, hi = ctx.spectral_bounds(steps=150)
+            lo, hi = ctx.spectral_bounds(steps=lanczos_steps)
             t_lanczos = time.perf_counter() - t0
-            g, e, rho = apc.apc_optimal_params(0.98 * lo, min(1.0, 1.01 * hi))
+            g, e, rho = apc.apc_optimal_params(lo_margin * lo, min(1.0, 1.01 * hi))
             ctx.solve(g, e, tol=tol, max_iters=100, check_every=50, refine=refine, raise_on_error=False)  # warm-up
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -608,6 +623,10 @@ def summarize(extra):
             out[f"tts_n32768_{key}_solve_s"] = get(t, key, "seconds")
             out[f"tts_n32768_{key}_total_s"] = get(t, key, "total_s")
             out[f"tts_n32768_{key}_rel_residual"] = get(t, key, "rel_residual")
+    for key in sorted(k for k in extra if k.startswith("tts_dc")):
+        for run in ("bf16_ir", "f32_ir"):
+            out[f"{key}_{run}_total_s"] = get(extra, key, run, "total_s")
+            out[f"{key}_{run}_converged"] = get(extra, key, run, "converged")
     if "batch" in extra:
         out["batch_ms_per_iter"] = get(extra, "batch", "ms_per_iter")
         out["batch_hbm_frac"] = get(extra, "batch", "roofline", "frac")
@@ -728,6 +747,18 @@ def run_ours(args):
             extra["tts_n32768"] = time_to_tolerance_large(dev)
         except Exception as exc:
             extra["tts_n32768"] = {"error": str(exc)}
+        for c in args.tts_dc:
+            key = f"tts_dc{c:g}"
+            # With D_c over 10^-1..10^1 the spectrum of X is dense near mu_min
+            # (kappa(X) ~ 2.6e5) and 150 Lanczos steps overestimate mu_min
+            # tenfold: more steps and a wider margin below the smallest Ritz value.
+            steps, margin = (150, 0.98) if c <= 0.5 else (800, 0.5)
+            try:
+                extra[key] = time_to_tolerance_large(dev, col_decades=c, max_iters=30000, plain=False,
+                                                     lanczos_steps=steps, lo_margin=margin)
+                extra[key]["lanczos_steps"], extra[key]["lo_margin"] = steps, margin
+            except Exception as exc:
+                extra[key] = {"error": str(exc)}
         try:
             extra["small_f64"] = time_small_f64(dev)
         except Exception as exc:
@@ -796,6 +827,8 @@ def main():
     p.add_argument("--cluster-size", type=int, default=0)
     p.add_argument("--fp32", type=int, default=1, help="also time the FP32 path on the same matrix")
     p.add_argument("--tts", type=int, default=1, help="also measure time to 1e-10 (BF16+IR vs FP32+IR)")
+    p.add_argument("--tts-dc", type=lambda v: [float(c) for c in v.split(",") if c], default=[0.5, 1.0],
+                   help="D_c ranges (decades, comma-separated) of the tall scaled time-to-tolerance legs")
     p.add_argument("--e2e", type=int, default=1)
     p.add_argument("--batch", type=int, default=1, help="also time the batched solver (256 systems, k = 32)")
     p.add_argument("--rhs", type=int, default=1, help="also time the differentiation workload (k = 16, T = 200)")

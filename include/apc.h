@@ -222,7 +222,10 @@ int apc_monitor(apc_ctx *ctx, double *rel_residual_host, void *stream);
  * the iteration runs as the inner solver of FP64 iterative refinement:
  * x <- x + delta, where delta is the APC solution of A delta = b - A x,
  * stopped when its residual (monitor, or FP64 for BF16) is below 1e-4 of
- * ||b - A x|| or stagnates; one FP64 residual per sweep.  The solution (FP64,
+ * ||b - A x|| or stagnates: it fell less than twofold over the iterations in
+ * which the best rate the parameters allow, sqrt|(gamma-1)(eta-1)| (Eq. 5;
+ * rho of Theorem 1), would make it fall tenfold (at least one check
+ * interval).  One FP64 residual per sweep.  The solution (FP64,
  * n) goes to x_dev.  Errors: NOT_CONVERGED (x_dev still holds the last
  * iterate), DIVERGED, PARAMS, TIMEOUT, CUDA. */
 int apc_solve(apc_ctx *ctx, double gamma, double eta, double tol, int64_t max_iters,

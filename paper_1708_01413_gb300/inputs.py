@@ -11,7 +11,9 @@ variants exercised by the solver):
 * ``gaussian_system``  A n x n with i.i.d. N(0,1) entries, x_true ~ N(0,1),
   b = A x_true.
 * ``scaled_system``    A = D_r G D_c, G i.i.d. N(0,1), D_r and D_c diagonal with
-  entries log-uniform in [10^-lo, 10^hi].
+  entries log-uniform in [10^-lo, 10^hi]; optionally tall (N > n rows) and with
+  D_c narrowed to [10^-c, 10^c] (row scaling leaves every block's row space,
+  hence X, unchanged; column scaling sets kappa(X)).
 * ``batch_systems``    independent systems with n ~ U{n_lo..n_hi},
   A = G + 0.5 sqrt(n) I, uneven row blocks p_i ~ U{p_lo..p_hi} (the last block
   truncated), k right-hand sides b ~ N(0,1).
@@ -51,12 +53,17 @@ def gaussian_system(n: int, seed: int, N: int | None = None, k: int = 1, mean: f
     return A, x_true, A @ x_true
 
 
-def scaled_system(n: int, seed: int, lo: float = 2.0, hi: float = 2.0):
-    """(A, x_true, b) with A = D_r G D_c, D entries log-uniform in [10^-lo, 10^hi]."""
+def scaled_system(n: int, seed: int, lo: float = 2.0, hi: float = 2.0, N: int | None = None,
+                  col_decades: float | None = None):
+    """(A, x_true, b) with A = D_r G D_c (N x n, N = n by default), D entries
+    log-uniform in [10^-lo, 10^hi]; ``col_decades`` = c narrows D_c to
+    [10^-c, 10^c] (D_r keeps the full range)."""
     rng = np.random.default_rng(seed)
-    G = rng.standard_normal((n, n))
-    d_r = 10.0 ** rng.uniform(-lo, hi, size=n)
-    d_c = 10.0 ** rng.uniform(-lo, hi, size=n)
+    N = n if N is None else N
+    G = rng.standard_normal((N, n))
+    d_r = 10.0 ** rng.uniform(-lo, hi, size=N)
+    c_lo, c_hi = (lo, hi) if col_decades is None else (col_decades, col_decades)
+    d_c = 10.0 ** rng.uniform(-c_lo, c_hi, size=n)
     A = (d_r[:, None] * G) * d_c[None, :]
     x_true = rng.standard_normal(n)
     return A, x_true, A @ x_true
@@ -100,13 +107,17 @@ def gaussian_system_torch(n: int, seed: int, device, dtype=None, N: int | None =
     return A, x_true, A @ x_true
 
 
-def scaled_system_torch(n: int, seed: int, device, lo: float = 2.0, hi: float = 2.0):
+def scaled_system_torch(n: int, seed: int, device, lo: float = 2.0, hi: float = 2.0, N: int | None = None,
+                        col_decades: float | None = None):
+    """Device draw of ``scaled_system``'s family (same arguments; a different stream)."""
     import torch
     g = torch.Generator(device=device)
     g.manual_seed(seed)
-    A = torch.randn((n, n), generator=g, device=device, dtype=torch.float64)
-    d_r = 10.0 ** (torch.rand((n,), generator=g, device=device, dtype=torch.float64) * (lo + hi) - lo)
-    d_c = 10.0 ** (torch.rand((n,), generator=g, device=device, dtype=torch.float64) * (lo + hi) - lo)
+    N = n if N is None else N
+    A = torch.randn((N, n), generator=g, device=device, dtype=torch.float64)
+    d_r = 10.0 ** (torch.rand((N,), generator=g, device=device, dtype=torch.float64) * (lo + hi) - lo)
+    c_lo, c_hi = (lo, hi) if col_decades is None else (col_decades, col_decades)
+    d_c = 10.0 ** (torch.rand((n,), generator=g, device=device, dtype=torch.float64) * (c_lo + c_hi) - c_lo)
     A.mul_(d_r[:, None]).mul_(d_c[None, :])
     x_true = torch.randn((n,), generator=g, device=device, dtype=torch.float64)
     return A, x_true, A @ x_true

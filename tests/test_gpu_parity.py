@@ -306,6 +306,25 @@ def test_refinement_reaches_1e10(prec):
     assert st["sweeps"] >= 2
 
 
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_refinement_on_tall_scaled_family(prec):
+    # The headline's family A = D_r G D_c made tall (N = 1.125 n), D_c narrowed
+    # to half a decade each way (kappa(X) ~ 6e3): parameters from the GPU
+    # Lanczos bounds, refinement to 1e-10 checked by the oracle's residual.
+    apc, dev = _apc(), _dev()
+    n, N = 2048, 2304
+    A, x_true, b = inputs.scaled_system(n, 21, N=N, col_decades=0.5)
+    offs = inputs.even_offsets(N, 9)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec)
+    lo, hi = ctx.spectral_bounds(steps=100)
+    assert 1e3 < hi / lo < 1e5
+    g, e, _ = apc.apc_optimal_params(0.98 * lo, min(1.0, 1.01 * hi))
+    x, st = ctx.solve(g, e, tol=1e-10, max_iters=20000, check_every=50, refine=True)
+    x = x.cpu().numpy()
+    assert st["rc"] == 0
+    assert O.relative_residual(A, b, x) <= 1e-10
+
+
 def test_tall_uneven_blocks_f64():
     # N > n (Sec. 2) with uneven contiguous blocks whose widths are not multiples of 32
     apc, dev = _apc(), _dev()
