@@ -59,7 +59,7 @@ typedef struct apc_ctx apc_ctx;
 typedef struct apc_options {
     int32_t precision;      /* APC_F64 / APC_F32 / APC_BF16                   */
     int32_t cluster_size;   /* CTAs sharing one row range, 1..8; 0 = automatic */
-    int32_t workers_per_warp; /* 1 or 2 blocks per warp; 0 = automatic        */
+    int32_t workers_per_warp; /* 1, 2 or 4 (FP32/BF16) blocks per warp; 0 = automatic */
     double  timeout_s;      /* limit of every device-side wait; 0 = 2 s       */
     int32_t rows_per_group; /* rows of Q per pipeline step, 1 or 2; 0 = automatic */
 } apc_options;

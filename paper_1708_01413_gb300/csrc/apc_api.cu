@@ -92,8 +92,14 @@ int configure(apc_ctx *c, int cs_request, int wpw_request, int rg_request) {
         for (int R = kMaxRowsPerGroup; R >= 1; --R) {
             if (rg_request > 0 && R != rg_request) continue;
             const int W0 = (c->m + cs - 1) / cs;
-            const int wpw = wpw_request > 0 ? wpw_request : (W0 >= 2 ? 2 : 1);
-            if (wpw < 1 || wpw > 2) continue;
+            // Four workers per element warp (8 element warps for 32 slots) when
+            // the CTA has at least 16: each warp's fixed cost per step (waits,
+            // barrier, addressing) is shared by more workers, and the control
+            // warps compete with fewer warps for issue slots.
+            const int wpw = wpw_request > 0 ? wpw_request
+                                            : (c->precision != APC_F64 && W0 >= 16) ? 4 : (W0 >= 2 ? 2 : 1);
+            if (wpw != 1 && wpw != 2 && wpw != 4) continue;
+            if (wpw == 4 && c->precision == APC_F64) continue;
             const int nw = (W0 + wpw - 1) / wpw;
             const int W = nw * wpw;  // worker slots per CTA
             if (W > 32 || nw > kMaxElemWarps || (cs - 1) * W >= c->m) continue;

@@ -2,8 +2,8 @@
 //
 // Work split.  The paper gives machine i the rows [A_i, b_i]; here the unknowns
 // j = 0..n-1 are split into contiguous row ranges, one per thread-block
-// cluster, and the m machines ("workers") into the CTAs of each cluster, one
-// or two workers per warp.  Q is stored [n][m][P]: row j holds, for every
+// cluster, and the m machines ("workers") into the CTAs of each cluster, one,
+// two or four workers per warp.  Q is stored [n][m][P]: row j holds, for every
 // worker i, the j-th row of Q_i (zero padded to P = 32*CPL columns).
 //
 // One pass over Q per iteration.  A cluster holds every worker's slice
@@ -244,7 +244,11 @@ __device__ __forceinline__ float2 df_from(double v) {
 }
 
 template <typename TQ, typename TS, int CPL, int WPW, bool kAPC, int R, bool kDet>
-__global__ void __launch_bounds__(kMaxThreads, 1) apc_iter_kernel(const IterArgs a) {
+// At most 32 worker slots per CTA: 32 / WPW element warps (16 for one worker
+// per warp) plus the control warps.  Four workers per warp run 8 element warps
+// with up to ~170 registers per thread.
+__global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlWarps) * 32, 1)
+    apc_iter_kernel(const IterArgs a) {
     static_assert(R == 1 || R == 2, "one or two rows per group");
     using TC = TS;
     constexpr bool kF64 = sizeof(TS) == 8;
@@ -773,6 +777,16 @@ void *kernel_for_rg(int cpl, int wpw, bool apc) {
             case 2: return APC_K(2, 2);
             case 4: return APC_K(4, 2);
             case 8: return APC_K(8, 2);
+        }
+    } else if (wpw == 4) {
+        // FP32 arithmetic only: FP64 z and z' for four workers would not fit
+        // the register budget of a 384-thread CTA
+        if constexpr (sizeof(TS) == 4) {
+            switch (cpl) {
+                case 2: return APC_K(2, 4);
+                case 4: return APC_K(4, 4);
+                case 8: return APC_K(8, 4);
+            }
         }
     }
 #undef APC_K

@@ -183,7 +183,7 @@ def test_f32_trajectory_matches_oracle(n, m, T):
     assert _rel(ctx.xbar().cpu().numpy(), ex.xbar) <= tol
 
 
-@pytest.mark.parametrize("cs,wpw", [(1, 1), (1, 2), (2, 2), (4, 1), (4, 2), (8, 2)])
+@pytest.mark.parametrize("cs,wpw", [(1, 1), (1, 2), (2, 2), (4, 1), (4, 2), (8, 2), (1, 4), (2, 4), (4, 4)])
 def test_cluster_sizes_agree(cs, wpw):
     # the same problem under every cluster size / workers per warp gives the oracle's trajectory
     apc, dev = _apc(), _dev()
