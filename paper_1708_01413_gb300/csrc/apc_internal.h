@@ -64,7 +64,8 @@ constexpr int kMaxElemWarps = 16;  // warps streaming Q per CTA of the iteration
 constexpr int kCtlWarps = 2 * kMaxRowsPerGroup;  // control warps per CTA (at most): per row of
                                    // a group, one for the master's update and one for the
                                    // machines' update
-constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps) * 32;
+constexpr int kProducerWarps = 1;  // issues the TMA copies of the Q ring
+constexpr int kMaxThreads = (kMaxElemWarps + kCtlWarps + kProducerWarps) * 32;
 
 // Kernel entry points, one translation unit per Q precision.
 void *iter_kernel_f64(int cpl, int wpw, bool apc, int rg);

@@ -22,7 +22,7 @@ cudaLaunchConfig_t make_config(int cs, int nw, int rg, int clusters, size_t smem
                                cudaLaunchAttribute *attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(clusters * cs), 1, 1);
-    cfg.blockDim = dim3(unsigned((nw + 2 * rg) * 32), 1, 1);
+    cfg.blockDim = dim3(unsigned((nw + 2 * rg + kProducerWarps) * 32), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;

@@ -245,9 +245,9 @@ __device__ __forceinline__ float2 df_from(double v) {
 
 template <typename TQ, typename TS, int CPL, int WPW, bool kAPC, int R, bool kDet>
 // At most 32 worker slots per CTA: 32 / WPW element warps (16 for one worker
-// per warp) plus the control warps.  Four workers per warp run 8 element warps
-// with up to ~170 registers per thread.
-__global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlWarps) * 32, 1)
+// per warp) plus the control warps and the producer warp.  Four workers per
+// warp run 8 element warps with up to ~150 registers per thread.
+__global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlWarps + kProducerWarps) * 32, 1)
     apc_iter_kernel(const IterArgs a) {
     static_assert(R == 1 || R == 2, "one or two rows per group");
     using TC = TS;
@@ -282,13 +282,17 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
     // coefficients; control warp R + r runs the machines' updates of row r of
     // group t, the CTA row sum and the cluster exchange.  The two chains are
     // independent within a step (they meet through shared memory two steps
-    // apart), so a step waits for the longer of them, not their sum.  Lane 0
-    // of control warp 1 issues TMA.
-    const bool is_ctl = warp >= nwe;
+    // apart), so a step waits for the longer of them, not their sum.  The last
+    // warp only produces: its lane 0 issues the TMA copies of the ring.  A
+    // bulk copy of a 16 KB row takes a few hundred cycles to issue, which on a
+    // control warp delayed that warp's chain by as much every step.
+    const bool is_ctl = warp >= nwe;  // every warp that is not an element warp
     const int ctl_r = warp - nwe;
     const int ctl_row = R == 2 ? (ctl_r & 1) : 0;
     const bool ctl_master = is_ctl && ctl_r < R;
-    const int issuer = (nwe + 1) * 32;
+    const bool ctl_update = is_ctl && ctl_r >= R && ctl_r < 2 * R;
+    const bool is_prod = ctl_r == 2 * R;
+    const int issuer = (nwe + 2 * R) * 32;
     const uint32_t rank = cluster_rank();
     const int cl = int(cluster_id_x());
     const int w0 = int(rank) * W;
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
     const bool c_act = is_ctl && lane < W_cta;
     TS *const cx0 = xw + size_t(row0 + ctl_row) * m + lane;
     const size_t xstep = size_t(R) * m;
-    const bool cx_ok = rx && c_act && !ctl_master;
+    const bool cx_ok = rx && c_act && ctl_update;
     TS *cx_next = cx0;
     int k_next = 0;
     auto cx_load_next = [&]() -> TS {
@@ -406,7 +410,7 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
         }
         return v;
     };
-    TS cxpre = (is_ctl && !ctl_master && G > 0) ? cx_load_next() : TS(0);
+    TS cxpre = (ctl_update && G > 0) ? cx_load_next() : TS(0);
     TS *cx_cur = cx0;
 
     uint32_t sb1 = 0, sb2 = 0;  // stage byte offsets: first product (group t), second (group t-3)
@@ -495,7 +499,9 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
             sb1 = uint32_t(st1) * stage_bytes;
         } else {
             const int r = ctl_row;
-            if (e1 && tid == issuer && W_cta > 0 && issued < total) issue_next();
+            if (is_prod) {
+                if (e1 && tid == issuer && W_cta > 0 && issued < total) issue_next();
+            }
             const int nrh2 = (t >= 2 && t - 2 < G) ? min(R, nrows - (t - 2) * R) : 0;
             if (ctl_master && mm) {
                 // ---- master of row r of group t-2: cluster row sums -> new xbar, coefficients ----
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
                     coefs[((g2 & 1) * 32 + lane) * R + r] = c;
                 }
             }
-            if (!ctl_master && e1) {
+            if (ctl_update && e1) {
                 // ---- machines' updates of row r of group t and the CTA row sum ----
                 TS xn = TS(0), contrib = TS(0);
                 if (r < nr && c_act) {
