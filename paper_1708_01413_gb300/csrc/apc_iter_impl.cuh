@@ -256,6 +256,9 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
     constexpr int VE = Elem<TQ>::V;
     constexpr int V = CPL < VE ? CPL : VE;  // elements per lane per vector
     constexpr int H = CPL / V;              // vectors per lane per row
+    constexpr int NV = WPW * R;             // dot products per element warp and step
+    constexpr int LNV = NV >= 8 ? 3 : NV >= 4 ? 2 : NV >= 2 ? 1 : 0;
+    static_assert(NV == 1 << LNV, "workers per warp times rows per group must be a power of two");
 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int abort_flag;
@@ -387,9 +390,11 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
             for (int h = 0; h < H; ++h)
                 qoff[sl][r][h] = uint32_t((r * L.row_stride + (warp * WPW + sl) * P + (h * 32 + lane) * V) * sizeof(TQ));
     const uint32_t stage_bytes = uint32_t(L.stage_elems * sizeof(TQ));
-    // element lane (r_l, s_l) publishes w_i of row r_l of worker slot warp*WPW + s_l
-    const int r_l = R == 2 ? lane >> 4 : 0, s_l = lane & 15;
-    const bool d_lane = !is_ctl && s_l < WPW && (R == 2 || lane < 16);
+    // after the butterfly, lane group k = lane >> (5 - LNV) holds dot product k
+    // (worker slot k / R, row k % R); its first lane publishes it
+    const int k_l = lane >> (5 - LNV);
+    const int r_l = k_l % R, s_l = k_l / R;
+    const bool d_lane = !is_ctl && (lane & ((32 >> LNV) - 1)) == 0;
     const int wl_d = warp * WPW + s_l;
 
     // ---- control warps: x_i of (row ctl_r, slot lane), one group ahead ----
@@ -431,10 +436,11 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
                     abort_code = DEV_TIMEOUT_TMA;
                 }
                 const unsigned char *stb = smem + sb1;
-                TC dsum[WPW];
+                // the lane's partial sums of the warp's NV = WPW * R dot products
+                // (k = slot * R + row)
+                TC dv[NV];
 #pragma unroll
                 for (int sl = 0; sl < WPW; ++sl) {
-                    TC dr[R];
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         TC d0 = TC(0), d1 = TC(0);
@@ -444,25 +450,27 @@ __global__ void __launch_bounds__(((WPW >= 2 ? 32 / WPW : kMaxElemWarps) + kCtlW
                             load_row<TQ, TC, V>(reinterpret_cast<const TQ *>(stb + qoff[sl][r][h]), qv);
                             dot_vec<TC, V>(d0, d1, qv, &z[sl][h * V]);
                         }
-                        dr[r] = d0 + d1;
+                        dv[sl * R + r] = d0 + d1;
                     }
-                    TC keep;
-                    if constexpr (R == 2) {
-                        // transposed butterfly: lanes 0-15 end with row 0, lanes 16-31 with row 1
-                        keep = (lane & 16) ? dr[1] : dr[0];
-                        const TC send = (lane & 16) ? dr[0] : dr[1];
-                        keep += __shfl_xor_sync(0xffffffffu, send, 16);
-                    } else {
-                        keep = dr[0] + __shfl_xor_sync(0xffffffffu, dr[0], 16);
-                    }
-#pragma unroll
-                    for (int off = 8; off > 0; off >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, off);
-                    dsum[sl] = keep;
                 }
-                TC myd = dsum[0];
+                // Transposed butterfly: at offsets 16, 8, ... each lane keeps half
+                // of its values and receives its partner's partial sums of them,
+                // so NV sums over 32 lanes take NV - 1 + 5 - log2(NV) shuffles
+                // (one sum per lane group of 32 / NV lanes at the end).
 #pragma unroll
-                for (int sl = 1; sl < WPW; ++sl) myd = (s_l == sl) ? dsum[sl] : myd;
-                if (d_lane) dsh[((g & 1) * R + r_l) * 32 + wl_d] = myd;
+                for (int lv = 0; lv < LNV; ++lv) {
+                    const int half = NV >> (lv + 1);
+                    const bool up = (lane >> (4 - lv)) & 1;
+#pragma unroll
+                    for (int k = 0; k < half; ++k) {
+                        const TC keep = up ? dv[k + half] : dv[k];
+                        const TC send = up ? dv[k] : dv[k + half];
+                        dv[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16 >> lv);
+                    }
+                }
+#pragma unroll
+                for (int off = 16 >> LNV; off > 0; off >>= 1) dv[0] += __shfl_xor_sync(0xffffffffu, dv[0], off);
+                if (d_lane) dsh[((g & 1) * R + r_l) * 32 + wl_d] = dv[0];
             }
         }
 
