@@ -103,6 +103,7 @@ constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, 
 
 struct SysDesc {
     const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
+    const __nv_bfloat16 *QB; // the same 4 KB pieces ordered for sweep B (see qb_block)
     float *X;                // x_i in blocks of 128 rows (see x_block)
     float2 *Xb;              // [kp][npad]  master estimate, double-float
     uint8_t *Xop;            // xbar' planes, B operand of sweep B (see op_offset), npad x 3kp BF16
@@ -148,6 +149,15 @@ __host__ __device__ __forceinline__ int tile_rows(int npad, int t) { return min(
 // first element of the basis block (tile t, window w): [tile_rows][64] BF16
 __host__ __device__ __forceinline__ size_t q_block(int Cq, int npad, int t, int w) {
     return size_t(t) * kTileRows * Cq + size_t(w) * tile_rows(npad, t) * kWin;
+}
+// Sweep B's copy of the basis: the [32 rows][64 columns] pieces of q_block
+// reordered so that a 32-row group's windows are contiguous, [tile][group of
+// 32 rows][window][32][64] (the same bytes, pre-swizzled alike).  A sweep-B
+// stage of up to 8 windows is then one bulk copy per 32 rows instead of one
+// per window (each copy costs the issuing thread 100+ cycles).
+// First element of the piece (row group G = row / 32, window w):
+__host__ __device__ __forceinline__ size_t qb_block(int Cq, int G, int w) {
+    return (size_t(G) * (Cq / kWin) + w) * 32 * kWin;
 }
 // first element of machine i's x_i block for rows 128 u .. 128 u + 127:
 // [kp][128] FP32 (the last block of a system padded to 128 rows with zeros)
@@ -706,12 +716,12 @@ __device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
         rs = rows_stage_b<MT>(nwin, pr.y, r0);
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
-        const int t = r0 / kTileRows, rr = r0 % kTileRows;
-        const uint32_t blk = uint32_t(rs) * kWin * 2;
-        mbar_arrive_expect_tx(&R.full[s], uint32_t(nwin) * blk + uint32_t(rs) * prow);
-        for (int j = 0; j < nwin; ++j)
-            tma_load_1d(R.qslot(s) + j * blk, d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin, blk,
-                        &R.full[s], policy);
+        // [group of 32 rows][window][32][64]: one copy of nwin pieces per group
+        const uint32_t gbytes = uint32_t(nwin) * 32 * kWin * 2;
+        mbar_arrive_expect_tx(&R.full[s], uint32_t(rs / 32) * gbytes + uint32_t(rs) * prow);
+        for (int gg = 0; gg < rs / 32; ++gg)
+            tma_load_1d(R.qslot(s) + gg * gbytes, d.QB + qb_block(d.Cq, r0 / 32 + gg, col0 / kWin), gbytes, &R.full[s],
+                        policy);
         tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xop + size_t(r0) * prow, uint32_t(rs) * prow, &R.full[s], policy);
         ++cur.q;
     }
@@ -786,14 +796,17 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
     const int2 pr = part_b<kSplit>(d, part);
     for (int r0 = pr.x, rs; r0 < pr.y; r0 += rs) {
         rs = rows_stage_b<MT>(nwin, pr.y, r0);
-        const uint32_t blk = uint32_t(rs) * kWin * 2;  // one [rs rows][64 columns] piece
+        // stage layout [group of 32 rows][window][32][64] (qb_block): 4 KB
+        // between windows (the M direction), nwin x 4 KB between 32-row groups
+        const uint32_t gbytes = uint32_t(nwin) * 4096u;
         const uint32_t s = cur.q % kQSlots;
         if (!wait_w(R, &R.full[s], (cur.q / kQSlots) & 1)) return;
         tc_fence_after();
         const uint32_t sq = smem_u32(R.qslot(s)), sx = sq + kSlotQBytes;
         for (int ks = 0; ks < rs / 16; ++ks) {
             for (int h = 0; h < nmt; ++h)
-                tc_mma_w(tmem + uint32_t(h * NB), smem_desc(sq + 2 * h * blk + ks * 2048, blk, 1024, 2),
+                tc_mma_w(tmem + uint32_t(h * NB),
+                         smem_desc(sq + 2 * h * 4096 + (ks >> 1) * gbytes + (ks & 1) * 2048, 4096, 1024, 2),
                        smem_desc(sx + ks * (NB * 32), 128, 256, 0), idesc, !first);
             first = false;
         }
@@ -1145,6 +1158,17 @@ __global__ void __launch_bounds__(kThreads, 1) apc_batch_kernel(const BatchArgs 
 }
 
 // ---- set-up kernels -----------------------------------------------------------------
+// QB (qb_block) from Q (q_block): block b copies piece (row group b / (Cq/64),
+// window b % (Cq/64)), 4 KB, as 256 x 16 bytes
+__global__ void qb_permute_kernel(const __nv_bfloat16 *Q, int npad, int Cq, __nv_bfloat16 *QB) {
+    const int nw = Cq / kWin;
+    const int G = int(blockIdx.x) / nw, w = int(blockIdx.x) % nw;
+    const int t = G * 32 / kTileRows, rr = G * 32 % kTileRows;
+    const uint4 *src = reinterpret_cast<const uint4 *>(Q + q_block(Cq, npad, t, w) + size_t(rr) * kWin);
+    uint4 *dst = reinterpret_cast<uint4 *>(QB + qb_block(Cq, G, w));
+    dst[threadIdx.x] = src[threadIdx.x];
+}
+
 // Qs [n][m][P] (single-system layout) -> the tile-major, pre-swizzled packed
 // basis: element (row j, packed column col) of block b = colblk[col / 16].
 __global__ void repack_kernel(const __nv_bfloat16 *Qs, int64_t n, int m, int P, const int *colblk,
@@ -1562,11 +1586,12 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         d.C = C;
         const size_t x_elems = x_block(m, kp, nxblocks, 0);
         int *d_co = nullptr, *d_cb = nullptr;
-        __nv_bfloat16 *Q = nullptr;
+        __nv_bfloat16 *Q = nullptr, *QB = nullptr;
         float *Cf = nullptr;
         double *Bc = nullptr;
         if ((rc = balloc(b, &d_co, sizeof(int) * (m + 1))) || (rc = balloc(b, &d_cb, sizeof(int) * (Cq / 16))) ||
             (rc = balloc(b, &Q, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
+            (rc = balloc(b, &QB, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
             (rc = balloc(b, &d.X, sizeof(float) * x_elems)) ||
             (rc = balloc(b, &d.Xb, sizeof(float2) * size_t(kp) * npad)) ||
             (rc = balloc(b, &d.Xop, size_t(npad) * kPlanesB * kp * 2)) ||
@@ -1576,6 +1601,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             (rc = balloc(b, &Bc, sizeof(double) * size_t(n) * k)))
             return bail(rc);
         d.Q = Q;
+        d.QB = QB;
         d.Ct = Cf;
         d.coloff = d_co;
         b->B.push_back(Bc);
@@ -1592,6 +1618,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         const unsigned grid = unsigned(std::min<int64_t>((npad * Cq + 255) / 256, 152 * 32));
         repack_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->Q), n, m, c->P, d_cb, d_co, c->d_p,
                                            int(npad), Cq, Q);
+        qb_permute_kernel<<<unsigned(npad / 32 * (Cq / kWin)), 256, 0, s>>>(Q, int(npad), Cq, QB);
         if (cudaGetLastError() != cudaSuccess) {
             bfail(b, APC_ERR_CUDA, "repack launch failed");
             return bail(APC_ERR_CUDA);
