@@ -103,7 +103,7 @@ constexpr int kTmemCols = 512;                      // sweep A: 4 x 2k columns, 
 
 struct SysDesc {
     const __nv_bfloat16 *Q;  // tile-major, pre-swizzled (see q_block)
-    const __nv_bfloat16 *QB; // the same 4 KB pieces ordered for sweep B (see qb_block)
+    const __nv_bfloat16 *QB; // the same 4 KB pieces ordered for sweep B (see qb_block), or null
     float *X;                // x_i in blocks of 128 rows (see x_block)
     float2 *Xb;              // [kp][npad]  master estimate, double-float
     uint8_t *Xop;            // xbar' planes, B operand of sweep B (see op_offset), npad x 3kp BF16
@@ -154,7 +154,10 @@ __host__ __device__ __forceinline__ size_t q_block(int Cq, int npad, int t, int 
 // reordered so that a 32-row group's windows are contiguous, [tile][group of
 // 32 rows][window][32][64] (the same bytes, pre-swizzled alike).  A sweep-B
 // stage of up to 8 windows is then one bulk copy per 32 rows instead of one
-// per window (each copy costs the issuing thread 100+ cycles).
+// per window (each copy costs the issuing thread 100+ cycles).  Built only
+// when the batch's bases are far larger than L2: when they fit, sweep B
+// re-reads from L2 what sweep A streamed, and a second copy would lose that
+// (one 8192 system, 134 MB: 44.7 -> 37.6 % L2 hits, forward 20 -> 24 ms).
 // First element of the piece (row group G = row / 32, window w):
 __host__ __device__ __forceinline__ size_t qb_block(int Cq, int G, int w) {
     return (size_t(G) * (Cq / kWin) + w) * 32 * kWin;
@@ -716,12 +719,23 @@ __device__ void sweep_b_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
         rs = rows_stage_b<MT>(nwin, pr.y, r0);
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
-        // [group of 32 rows][window][32][64]: one copy of nwin pieces per group
-        const uint32_t gbytes = uint32_t(nwin) * 32 * kWin * 2;
-        mbar_arrive_expect_tx(&R.full[s], uint32_t(rs / 32) * gbytes + uint32_t(rs) * prow);
-        for (int gg = 0; gg < rs / 32; ++gg)
-            tma_load_1d(R.qslot(s) + gg * gbytes, d.QB + qb_block(d.Cq, r0 / 32 + gg, col0 / kWin), gbytes, &R.full[s],
-                        policy);
+        if (d.QB) {
+            // sweep B's copy, [group of 32 rows][window][32][64]: one copy of
+            // nwin pieces per group
+            const uint32_t gbytes = uint32_t(nwin) * 32 * kWin * 2;
+            mbar_arrive_expect_tx(&R.full[s], uint32_t(rs / 32) * gbytes + uint32_t(rs) * prow);
+            for (int gg = 0; gg < rs / 32; ++gg)
+                tma_load_1d(R.qslot(s) + gg * gbytes, d.QB + qb_block(d.Cq, r0 / 32 + gg, col0 / kWin), gbytes,
+                            &R.full[s], policy);
+        } else {
+            // the shared basis: one [rs rows][64] piece per window
+            const int t = r0 / kTileRows, rr = r0 % kTileRows;
+            const uint32_t blk = uint32_t(rs) * kWin * 2;
+            mbar_arrive_expect_tx(&R.full[s], uint32_t(nwin) * blk + uint32_t(rs) * prow);
+            for (int j = 0; j < nwin; ++j)
+                tma_load_1d(R.qslot(s) + j * blk, d.Q + q_block(d.Cq, d.npad, t, col0 / kWin + j) + size_t(rr) * kWin,
+                            blk, &R.full[s], policy);
+        }
         tma_load_1d(R.qslot(s) + kSlotQBytes, d.Xop + size_t(r0) * prow, uint32_t(rs) * prow, &R.full[s], policy);
         ++cur.q;
     }
@@ -796,9 +810,12 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
     const int2 pr = part_b<kSplit>(d, part);
     for (int r0 = pr.x, rs; r0 < pr.y; r0 += rs) {
         rs = rows_stage_b<MT>(nwin, pr.y, r0);
-        // stage layout [group of 32 rows][window][32][64] (qb_block): 4 KB
-        // between windows (the M direction), nwin x 4 KB between 32-row groups
-        const uint32_t gbytes = uint32_t(nwin) * 4096u;
+        // stage layout, sweep B's copy (qb_block): [group of 32 rows][window][32][64],
+        // 4 KB between windows (the M direction), nwin x 4 KB between 32-row
+        // groups; the shared basis: [window][rs rows][64], rs x 128 bytes
+        // between windows
+        const uint32_t wstr = d.QB ? 4096u : uint32_t(rs) * 128u;
+        const uint32_t gbytes = d.QB ? uint32_t(nwin) * 4096u : 4096u;
         const uint32_t s = cur.q % kQSlots;
         if (!wait_w(R, &R.full[s], (cur.q / kQSlots) & 1)) return;
         tc_fence_after();
@@ -806,7 +823,7 @@ __device__ void sweep_b_mma(const Ring &R, Cursor &cur, uint32_t &ubc, uint64_t 
         for (int ks = 0; ks < rs / 16; ++ks) {
             for (int h = 0; h < nmt; ++h)
                 tc_mma_w(tmem + uint32_t(h * NB),
-                         smem_desc(sq + 2 * h * 4096 + (ks >> 1) * gbytes + (ks & 1) * 2048, 4096, 1024, 2),
+                         smem_desc(sq + 2 * h * wstr + (ks >> 1) * gbytes + (ks & 1) * 2048, wstr, 1024, 2),
                        smem_desc(sx + ks * (NB * 32), 128, 256, 0), idesc, !first);
             first = false;
         }
@@ -1535,6 +1552,24 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
     const int MT = b->MT, kp = b->kp;
     const int64_t *offs = row_offsets_host;
     int rc = APC_OK;
+    // sweep B's copy of the bases (qb_block) when all packed bases together
+    // exceed twice the L2 cache
+    bool use_qb = false;
+    {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->device);
+        int64_t total = 0;
+        const int64_t *o = row_offsets_host;
+        for (int sys = 0; sys < nsys; ++sys) {
+            const int m = m_host[sys];
+            if (m < 1) break;  // rejected in the loop below
+            int64_t C = 0;
+            for (int i = 0; i < m; ++i) C += (o[i + 1] - o[i] + 15) / 16 * 16;
+            total += int64_t(2) * ((n_host[sys] + 31) / 32 * 32) * ((C + kWin - 1) / kWin * kWin);
+            o += m + 1;
+        }
+        use_qb = l2 > 0 && total > int64_t(2) * l2;
+    }
     for (int sys = 0; sys < nsys; ++sys) {
         const int64_t n = n_host[sys];
         const int m = m_host[sys];
@@ -1543,8 +1578,8 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
             bfail(b, APC_ERR_INVALID_ARG, "system %d: bad size, pointer or offsets", sys);
             return bail(APC_ERR_INVALID_ARG);
         }
-        // FP64 set-up of the single-system solver: row scaling and two passes
-        // of Cholesky QR per block (Sec. 3.3); Q_i rounded to BF16 once
+        // FP64 set-up of the single-system solver: row scaling and Cholesky QR
+        // per block (Sec. 3.3); Q_i rounded to BF16 once
         if (bcol) cudaFree(bcol);
         bcol = nullptr;
         if (cudaMalloc(&bcol, sizeof(double) * n) != cudaSuccess) {
@@ -1591,7 +1626,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         double *Bc = nullptr;
         if ((rc = balloc(b, &d_co, sizeof(int) * (m + 1))) || (rc = balloc(b, &d_cb, sizeof(int) * (Cq / 16))) ||
             (rc = balloc(b, &Q, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
-            (rc = balloc(b, &QB, sizeof(__nv_bfloat16) * size_t(npad) * Cq)) ||
+            (use_qb && (rc = balloc(b, &QB, sizeof(__nv_bfloat16) * size_t(npad) * Cq))) ||
             (rc = balloc(b, &d.X, sizeof(float) * x_elems)) ||
             (rc = balloc(b, &d.Xb, sizeof(float2) * size_t(kp) * npad)) ||
             (rc = balloc(b, &d.Xop, size_t(npad) * kPlanesB * kp * 2)) ||
@@ -1618,7 +1653,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         const unsigned grid = unsigned(std::min<int64_t>((npad * Cq + 255) / 256, 152 * 32));
         repack_kernel<<<grid, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(c->Q), n, m, c->P, d_cb, d_co, c->d_p,
                                            int(npad), Cq, Q);
-        qb_permute_kernel<<<unsigned(npad / 32 * (Cq / kWin)), 256, 0, s>>>(Q, int(npad), Cq, QB);
+        if (use_qb) qb_permute_kernel<<<unsigned(npad / 32 * (Cq / kWin)), 256, 0, s>>>(Q, int(npad), Cq, QB);
         if (cudaGetLastError() != cudaSuccess) {
             bfail(b, APC_ERR_CUDA, "repack launch failed");
             return bail(APC_ERR_CUDA);
