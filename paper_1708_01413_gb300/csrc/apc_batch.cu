@@ -163,9 +163,12 @@ __host__ __device__ __forceinline__ size_t qb_block(int Cq, int G, int w) {
     return (size_t(G) * (Cq / kWin) + w) * 32 * kWin;
 }
 // first element of machine i's x_i block for rows 128 u .. 128 u + 127:
-// [kp][128] FP32 (the last block of a system padded to 128 rows with zeros)
-__host__ __device__ __forceinline__ size_t x_block(int m, int kp, int u, int i) {
-    return (size_t(u) * m + i) * kp * kXRows;
+// [kp][128] FP32 (the last block of a system padded to 128 rows with zeros).
+// A machine's blocks are contiguous (nxs = blocks per machine, n_pad / 128
+// rounded up), so a 256-row unit's x_i tile is one bulk copy.
+__host__ __device__ __forceinline__ int x_blocks(int npad) { return (npad + kXRows - 1) / kXRows; }
+__host__ __device__ __forceinline__ size_t x_block(int nxs, int kp, int u, int i) {
+    return (size_t(i) * nxs + u) * kp * kXRows;
 }
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -442,6 +445,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     const int w_lo = pa.c_lo >> 2, w_hi = (pa.c_hi + 3) >> 2;  // windows holding the part's chunks
     const uint32_t qbytes = uint32_t(rows) * kWin * 2, zbytes = kPlanesA * KP * 128;
     const int u0 = row0 / kXRows, nxb = (rows + kXRows - 1) / kXRows;  // x_i blocks of 128 rows per machine
+    const int nxs = x_blocks(d.npad);
     const uint32_t xblk = uint32_t(KP) * kXRows * 4;
     auto qsrc = [&](int w) { return d.Q + q_block(d.Cq, d.npad, t, w) + size_t(ro) * kWin; };
     int pi = pa.i_lo;  // next machine whose x_i tile is due
@@ -452,7 +456,7 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
     for (int w = w_lo; w < min(w_lo + pf, w_hi); ++w) prefetch_l2(qsrc(w), qbytes);
     if (!no_x)
         for (int i = pa.i_lo; i < min(pa.i_lo + pf, pa.i_hi); ++i)
-            for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, i), xblk);
+            prefetch_l2(d.X + x_block(nxs, KP, u0, i), uint32_t(nxb) * xblk);
     for (int w = w_lo; w < w_hi; ++w) {
         const uint32_t s = cur.q % kQSlots;
         if (!acquire_slot(R, R.empty, kQSlots, cur.q)) return;
@@ -466,10 +470,9 @@ __device__ void sweep_a_producer(const Ring &R, Cursor &cur, const SysDesc &d, i
             const uint32_t xs = cur.x % kXSlots;
             if (!acquire_slot(R, R.xempty, kXSlots, cur.x)) return;
             mbar_arrive_expect_tx(&R.xfull[xs], uint32_t(nxb) * xblk);
-            for (int j = 0; j < nxb; ++j)
-                tma_load_1d(R.xslot(xs) + j * xblk, d.X + x_block(d.m, KP, u0 + j, pi), xblk, &R.xfull[xs], policy);
+            tma_load_1d(R.xslot(xs), d.X + x_block(nxs, KP, u0, pi), uint32_t(nxb) * xblk, &R.xfull[xs], policy);
             if (pi + pf < pa.i_hi)
-                for (int j = 0; j < nxb; ++j) prefetch_l2(d.X + x_block(d.m, KP, u0 + j, pi + pf), xblk);
+                prefetch_l2(d.X + x_block(nxs, KP, u0, pi + pf), uint32_t(nxb) * xblk);
             ++cur.x;
             ++pi;
         }
@@ -612,7 +615,7 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
             // the x_i tile holds [kp][128] blocks of 128 rows: the row's value
             // for right-hand side q sits 512 q bytes after its first one
             const uint32_t sxr = sx + uint32_t(h) * uint32_t(KP * kXRows * 4) + uint32_t(r & (kXRows - 1)) * 4u;
-            float *xg = d.X + x_block(d.m, KP, (row0 >> 7) + h, i) + (r & (kXRows - 1));
+            float *xg = d.X + x_block(x_blocks(d.npad), KP, (row0 >> 7) + h, i) + (r & (kXRows - 1));
 #pragma unroll
             for (int q = 0; q < KP; ++q) {
                 const float xo = init ? 0.0f : lds_f32(sxr + uint32_t(q) * (kXRows * 4));
@@ -1248,7 +1251,7 @@ __global__ void x_out_kernel(const float *X, int64_t n, int npad, int m, int kp,
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
         const int j = int(i / k);
         const int r = int(i - int64_t(j) * k);
-        const size_t off = x_block(m, kp, j / kXRows, worker) + size_t(r) * kXRows + j % kXRows;
+        const size_t off = x_block(x_blocks(npad), kp, j / kXRows, worker) + size_t(r) * kXRows + j % kXRows;
         out[int64_t(j) * ldx + r] = double(X[off]);
     }
 }
@@ -1619,7 +1622,7 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
         d.m = m;
         d.Cq = Cq;
         d.C = C;
-        const size_t x_elems = x_block(m, kp, nxblocks, 0);
+        const size_t x_elems = x_block(nxblocks, kp, 0, m);
         int *d_co = nullptr, *d_cb = nullptr;
         __nv_bfloat16 *Q = nullptr, *QB = nullptr;
         float *Cf = nullptr;
