@@ -59,8 +59,10 @@ int apc_batch_setup(apc_batch **out, int32_t nsys, const int64_t *n_host, const 
 
 /* apc_batch_set_params -- (gamma_s, eta_s) per system, host arrays of nsys
  * (Theorem 1 gives the optimal pair from the extreme eigenvalues of X_s, see
- * apc_optimal_params).  Errors: PARAMS unless 0 < gamma_s < 2 and eta_s is
- * finite (nothing is changed then), INVALID_ARG, CUDA. */
+ * apc_optimal_params).  Synchronous: the parameters are copied to the device
+ * with a blocking copy, which waits for the device's earlier work.  Errors:
+ * PARAMS unless 0 < gamma_s < 2 and eta_s is finite (nothing is changed
+ * then), INVALID_ARG, CUDA. */
 int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *eta_host);
 
 /* apc_batch_set_hb_params -- switch later apc_batch_iterate calls to the
@@ -72,8 +74,9 @@ int apc_batch_set_params(apc_batch *b, const double *gamma_host, const double *e
  * (the D-HBM update of Sec. 4.3), with x the master's estimate
  * (apc_batch_get_xbar) and zeta = 0 after apc_batch_reset.  alpha_host and
  * beta_host hold one value per system (see apc_hb_optimal_params).
- * apc_batch_set_params switches back to APC.  Errors: PARAMS unless
- * alpha > 0 and 0 <= beta < 1 (nothing is changed then), INVALID_ARG, CUDA. */
+ * apc_batch_set_params switches back to APC.  Synchronous, like
+ * apc_batch_set_params.  Errors: PARAMS unless alpha > 0 and 0 <= beta < 1
+ * (nothing is changed then), INVALID_ARG, CUDA. */
 int apc_batch_set_hb_params(apc_batch *b, const double *alpha_host, const double *beta_host);
 
 /* apc_batch_reset -- Algorithm 1 initialisation of every system (and a zero

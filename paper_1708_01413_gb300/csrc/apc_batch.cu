@@ -2117,9 +2117,17 @@ int multi_rhs_batch(apc_ctx *c, int64_t k, double gamma, double eta, cudaStream_
         // against 0.35 ms with the many-system default)
         const int rc2 = apc_batch_set_tiles(c->mrhs, 256, 256, 1, 0, 4, 4);
         if (rc2 != APC_OK) return cfail(c, rc2, "%s", apc_batch_last_error(c->mrhs));
+        c->mrhs_params_set = false;
     }
-    const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);
-    if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));
+    // the parameters' upload is synchronous: repeat it only when they change,
+    // so that calls with the same (gamma, eta) queue back to back on the stream
+    if (!c->mrhs_params_set || gamma != c->mrhs_gamma || eta != c->mrhs_eta) {
+        const int rc = apc_batch_set_params(c->mrhs, &gamma, &eta);
+        if (rc != APC_OK) return cfail(c, rc, "%s", apc_batch_last_error(c->mrhs));
+        c->mrhs_gamma = gamma;
+        c->mrhs_eta = eta;
+        c->mrhs_params_set = true;
+    }
     return APC_OK;
 }
 
@@ -2133,6 +2141,7 @@ void destroy_multi_rhs(apc_ctx *c) {
     c->mrhs = nullptr;
     c->mrhs_in = c->mrhs_out = nullptr;
     c->mrhs_k = 0;
+    c->mrhs_params_set = false;
 }
 }  // namespace apc
 

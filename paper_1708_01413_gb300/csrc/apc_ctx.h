@@ -38,6 +38,8 @@ struct apc_ctx {
     // square context): a one-system batch on the tensor cores, built on first use
     struct apc_batch *mrhs = nullptr;
     int mrhs_k = 0;
+    double mrhs_gamma = 0.0, mrhs_eta = 0.0;  // the parameters last uploaded to mrhs
+    bool mrhs_params_set = false;
     double *mrhs_in = nullptr, *mrhs_out = nullptr;  // n x k staging, leading dimension k
     std::string last_error;
 };
