@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <utility>
 #include <vector>
@@ -661,7 +662,7 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
             window = std::min(window, std::max(check_every, int64_t(std::ceil(std::log(0.1) / std::log(best_rate)))));
         else if (best_rate == 0.0)
             window = check_every;
-        std::vector<std::pair<int64_t, double>> hist;
+        std::deque<std::pair<int64_t, double>> hist;  // (iterations, inner residual) of the sweep's checks
         while (iters < max_iters && sweeps < max_sweeps) {
             if (rel <= tol) { rc = APC_OK; break; }
             ++sweeps;
@@ -693,10 +694,10 @@ int apc_solve(apc_ctx *c, double gamma, double eta, double tol, int64_t max_iter
                 }
                 if (!std::isfinite(inner)) return fail(c, APC_ERR_NONFINITE, "inner iterate became non-finite");
                 if (inner > 1e8) return fail(c, APC_ERR_DIVERGED, "inner residual grew to %g", inner);
-                // the latest check at least `window` iterations back
-                double back = -1.0;
-                for (const auto &h : hist)
-                    if (iters - h.first >= window) back = h.second;
+                // the latest check at least `window` iterations back (older
+                // ones are no longer needed)
+                while (hist.size() >= 2 && iters - hist[1].first >= window) hist.pop_front();
+                const double back = (!hist.empty() && iters - hist.front().first >= window) ? hist.front().second : -1.0;
                 hist.push_back({iters, inner});
                 const bool stalled = back > 0.0 && inner > 0.5 * back && inner < 0.5 && iters - sweep_start >= window;
                 if (inner <= 1e-4 || stalled || rel * inner <= 0.5 * tol) break;
