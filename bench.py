@@ -458,8 +458,9 @@ def time_fp32(A, b, offs, gamma, eta, T, peak, stream):
 def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None, tiles="tune"):
     """The batched solver (one persistent launch of `iters` iterations per
     step) on the 256-system workload.  Algorithmic bytes per iteration: the
-    packed BF16 bases read twice (one product each) and the machines'
-    iterates read and written once."""
+    packed BF16 bases read twice (one product each), the machines' iterates
+    and the master's estimate read and written once (heavy ball: estimate and
+    momentum, no machines' iterates)."""
     import numpy as np
     import torch
     from paper_1708_01413_gb300 import apc, inputs
@@ -507,12 +508,16 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None,
     sec_hb = hb0.elapsed_time(hb1) / 1e3 / (reps * iters)
     # algorithmic bytes without the kernel's padding (rows to 32, each block's
     # columns to 16, right-hand sides to kp): Q_s is n_s x n_s BF16 (the blocks
-    # of a square system hold n_s rows in all), x_i is n_s x k FP32 per machine
+    # of a square system hold n_s rows in all), x_i is n_s x k FP32 per machine,
+    # the master's estimate n_s x k double-float (8 bytes); each read and
+    # written once per iteration (heavy ball: estimate and momentum, no x_i)
     ns = np.array([n for n, _ in specs], dtype=np.float64)
     ms = np.array([len(o) - 1 for _, o in specs], dtype=np.float64)
     q_alg = float((ns ** 2).sum()) * 2
     x_alg = float((ms * ns).sum()) * k * 4
-    alg = 2 * q_alg + 2 * x_alg
+    xb_alg = float(ns.sum()) * k * 8
+    alg = 2 * q_alg + 2 * x_alg + 2 * xb_alg
+    alg_hb = 2 * q_alg + 4 * xb_alg
     padded = 2 * info["q_bytes"] + 2 * info["state_bytes"]
     kp = 16 if k <= 16 else 32
     cq = info["q_bytes"] / 2.0  # sum over systems of npad * Cq
@@ -531,9 +536,9 @@ def time_batch(dev, peak, stream, iters=50, reps=3, nsys=256, k=32, clocks=None,
                          "algorithmic_bytes_per_iter": alg, "traffic_model_padded_bytes_per_iter": padded,
                          "kernel": "apc_batch_kernel", "tensor_tflops": mma_flops / sec / 1e12},
             "heavy_ball": {"ms_per_iter": sec_hb * 1e3, "iter_per_s": 1.0 / sec_hb,
-                           "achieved_gbs": 2 * q_alg / sec_hb / 1e9,
-                           "frac": 2 * q_alg / sec_hb / 1e9 / peak,
-                           "algorithmic_bytes_per_iter": 2 * q_alg}}
+                           "achieved_gbs": alg_hb / sec_hb / 1e9,
+                           "frac": alg_hb / sec_hb / 1e9 / peak,
+                           "algorithmic_bytes_per_iter": alg_hb}}
 
 
 def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
@@ -544,7 +549,8 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
     FP32 context: column after column through the iteration kernel.
     Algorithmic bytes per tensor-core iteration: the packed BF16 basis read
     twice (one product each, n x n x 2 bytes unpadded) plus the machines'
-    iterates read and written (forward only: m n k x 4 bytes twice); the
+    iterates read and written (forward only: m n k x 4 bytes twice) and the
+    master's estimate read and written (double-float, 16 n k bytes); the
     reverse sweep has no per-machine state (every machine's adjoint is one
     shared vector), only its n x k row state (double-float ell and lbar, read
     and written: 32 n k bytes)."""
@@ -586,7 +592,7 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
             r = {"forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "total_ms": (fwd + bwd) * 1e3}
             if prec == "bf16":
                 q = 2.0 * n * n
-                fb, bb = 2 * q + 2 * m * n * k * 4, 2 * q + 32 * n * k
+                fb, bb = 2 * q + 2 * m * n * k * 4 + 16 * n * k, 2 * q + 32 * n * k
                 r.update({"path": "tensor cores (tcgen05), k columns together",
                           "forward_gbs": fb * T / fwd / 1e9, "forward_frac": fb * T / fwd / 1e9 / peak,
                           "backward_gbs": bb * T / bwd / 1e9, "backward_frac": bb * T / bwd / 1e9 / peak,
