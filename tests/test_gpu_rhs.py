@@ -108,6 +108,29 @@ def test_forward_and_backward_rhs_in_one_call(prec):
         assert _rel(DB, want) <= 1e-10
 
 
+def test_rhs_parameters_change_between_calls():
+    # one BF16 context, calls with (gamma1, eta1), then (gamma2, eta2), then
+    # (gamma1, eta1) again: every call follows its own parameters (the batch's
+    # parameters are uploaded again only when they change), forward and reverse
+    apc, dev = _env()
+    n, m, k, T = 512, 4, 5, 20
+    A, _, _ = inputs.gaussian_system(n, 63)
+    rng = np.random.default_rng(14)
+    B = rng.standard_normal((n, k))
+    G = rng.standard_normal((n, k))
+    offs = inputs.even_offsets(n, m)
+    Qs, Rs = _oracle_system(A, offs)
+    g1, e1, _ = O.optimal_params(*O.mu_bounds(Qs))
+    g2, e2 = 0.8, 1.3
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(B[:, 0].copy(), device=dev), offs, precision="bf16")
+    Bt, Gt = torch.tensor(B, device=dev), torch.tensor(G, device=dev)
+    for g, e in ((g1, e1), (g2, e2), (g2, e2), (g1, e1)):
+        X = ctx.forward_rhs(Bt, T, g, e).cpu().numpy()
+        DB = ctx.backward_rhs(Gt, T, g, e).cpu().numpy()
+        assert _rel(X, _affine_forward(Qs, Rs, offs, B, g, e, T)) <= 1e-4
+        assert _rel(DB, _affine_backward(Qs, Rs, G, g, e, T)) <= 1e-4
+
+
 def test_differentiation_workload_on_tensor_cores_full_size():
     # The differentiation workload (A 8192 x 8192 Gaussian, m = 32 blocks of
     # 256, k = 16, T = 200) through APCSolveFn on a BF16 context: one call per
