@@ -150,6 +150,25 @@ def _dist():
     return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0"))
 
 
+def max_over_ranks(x, device=None):
+    """The largest x over the ranks of the default process group, after a
+    barrier (x itself without one): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, max_ms):
+    """Whole-job throughput of `world` replicas that each processed
+    `units_per_rank` units, timed by the slowest rank (weak scaling)."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def _threads():
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
         if os.environ.get(k):
@@ -688,13 +707,8 @@ def run_ours(args):
             ev[s][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        torch.distributed.barrier()
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = args.steps * T * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dev)
+    value = job_rate(args.steps * T, world, total_ms)
 
     # roofline of the iteration kernel: algorithmic bytes per launch / launch time.
     # Per iteration: Q once, x_i read + written (FP32 or FP64), xbar read + written.
