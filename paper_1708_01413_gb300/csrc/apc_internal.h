@@ -26,8 +26,8 @@ struct IterArgs {
     int64_t n;
     int32_t m, P;
     int32_t cs;         // cluster size (CTAs sharing a row range)
-    int32_t nw;         // warps per CTA
-    int32_t wpw;        // workers per warp (1 or 2); worker slots per CTA = nw * wpw
+    int32_t nw;         // element warps per CTA
+    int32_t wpw;        // workers per element warp (1, 2 or 4); worker slots per CTA = nw * wpw
     int32_t rg;         // rows of Q per pipeline step (1 or 2); 2 * rg control warps
     int32_t stages;     // TMA ring depth
     int32_t mode;
