@@ -138,7 +138,28 @@ int configure(apc_ctx *c, int cs_request, int wpw_request, int rg_request) {
                 c->P, (long long)c->n, cs_request, wpw_request, rg_request);
 }
 
-int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
+// Device-side wait that timed out, if any (then cleared): APC_OK or TIMEOUT.
+// Synchronises the stream.
+int check_device_error(apc_ctx *c, cudaStream_t s) {
+    int herr = 0;
+    CK(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (herr != 0) {
+        cudaMemsetAsync(c->err, 0, sizeof(int), s);
+        cudaStreamSynchronize(s);
+        static const char *what[] = {"", "TMA stage", "cluster exchange", "grid barrier"};
+        return fail(c, APC_ERR_TIMEOUT, "device wait timed out (%s)", what[herr >= 1 && herr <= 3 ? herr : 0]);
+    }
+    return APC_OK;
+}
+
+// `iters` passes of the iteration kernel in `mode`.  With check (the public
+// calls) the stream is synchronised after each launch and a device-side
+// timeout is reported at once; without it the launches only queue (a caller
+// that runs many short passes, the Lanczos process, checks once at its end
+// with check_device_error; every wait in the kernel is bounded, so passes
+// after a timed-out one still end).
+int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s, bool check = true) {
     const int64_t chunk_max = 1 << 20;
     while (iters > 0) {
         const int64_t it = std::min(iters, chunk_max);
@@ -180,14 +201,9 @@ int run_pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cuda
         if (e != cudaSuccess) return fail(c, APC_ERR_LAUNCH, "iteration kernel launch failed: %s", cudaGetErrorString(e));
         c->t += it;
         iters -= it;
-        int herr = 0;
-        CK(c, cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CK(c, cudaStreamSynchronize(s));
-        if (herr != 0) {
-            cudaMemsetAsync(c->err, 0, sizeof(int), s);
-            cudaStreamSynchronize(s);
-            static const char *what[] = {"", "TMA stage", "cluster exchange", "grid barrier"};
-            return fail(c, APC_ERR_TIMEOUT, "device wait timed out (%s)", what[herr >= 1 && herr <= 3 ? herr : 0]);
+        if (check) {
+            const int rc = check_device_error(c, s);
+            if (rc != APC_OK) return rc;
         }
     }
     return APC_OK;
@@ -233,6 +249,10 @@ void set_global_error_text(const char *msg) { g_setup_error = msg; }
 int pass(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
     return run_pass(c, mode, gamma, eta, iters, s);
 }
+int pass_queued(apc_ctx *c, int mode, double gamma, double eta, int64_t iters, cudaStream_t s) {
+    return run_pass(c, mode, gamma, eta, iters, s, false);
+}
+int device_error(apc_ctx *c, cudaStream_t s) { return check_device_error(c, s); }
 }  // namespace apc
 
 extern "C" {
