@@ -598,17 +598,19 @@ def time_rhs(dev, peak, stream, n=8192, m=32, k=16, T=200, reps=3, tune=True):
             ctx.backward_rhs(G, T, gam, eta)
             torch.cuda.synchronize()
             f0, f1, b1 = _ev(), _ev(), _ev()
-            f0.record(stream)
-            for _ in range(reps):
-                ctx.forward_rhs(B, T, gam, eta, out=X)
-            f1.record(stream)
-            for _ in range(reps):
-                ctx.backward_rhs(G, T, gam, eta)
-            b1.record(stream)
-            torch.cuda.synchronize()
+            with ClockSampler(torch.cuda.current_device()) as clk:
+                f0.record(stream)
+                for _ in range(reps):
+                    ctx.forward_rhs(B, T, gam, eta, out=X)
+                f1.record(stream)
+                for _ in range(reps):
+                    ctx.backward_rhs(G, T, gam, eta)
+                b1.record(stream)
+                torch.cuda.synchronize()
             fwd = f0.elapsed_time(f1) / reps / 1e3
             bwd = f1.elapsed_time(b1) / reps / 1e3
-            r = {"forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "total_ms": (fwd + bwd) * 1e3}
+            r = {"forward_ms": fwd * 1e3, "backward_ms": bwd * 1e3, "total_ms": (fwd + bwd) * 1e3,
+                 "clocks": clk.summary()}
             if prec == "bf16":
                 q = 2.0 * n * n
                 fb, bb = 2 * q + 2 * m * n * k * 4 + 16 * n * k, 2 * q + 32 * n * k
