@@ -408,6 +408,20 @@ def test_backward_matches_oracle_adjoint(prec, tol):
     ctx.iterate(g, e, 5)
 
 
+def test_backward_with_four_workers_per_warp():
+    # the reverse sweep's generic pass modes with 32 blocks in one CTA and four
+    # workers per element warp (FP32 context), against the FP64 oracle sweep
+    apc, dev = _apc(), _dev()
+    n, m, T = 2048, 32, 30
+    A, x_true, b, offs, blocks, Qs, Rs, g, e = _case(n, m, 16)
+    gT = inputs.target_vector(n, 16)
+    ref = np.concatenate(O.apc_adjoint(blocks, Qs, Rs, g, e, T, gT)[0])
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision="f32",
+                        workers_per_warp=4)
+    db = ctx.backward(torch.tensor(gT, device=dev), T, g, e).cpu().numpy()
+    assert _rel(db, ref) <= 1e-4
+
+
 @pytest.mark.parametrize("prec,ck,tol", [("f64", 1, 1e-9), ("f64", 7, 1e-9), ("f64", 0, 1e-9), ("f64", 40, 1e-9),
                                          ("f32", 0, 2e-3)])
 def test_backward_params_match_oracle(prec, ck, tol):

@@ -85,3 +85,22 @@ def test_gpu_bounds_drive_a_solve_to_1e10():
     g0, e0, _ = O.optimal_params(lo, hi)
     x0, st0 = ctx.solve(g0, e0, tol=1e-10, max_iters=200000, check_every=100)
     assert st["iterations"] <= 4 * st0["iterations"] + 200
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f32"])
+def test_lanczos_with_four_workers_per_warp(prec):
+    # 32 blocks in one CTA with four workers per element warp (the automatic
+    # choice for FP32/BF16 at 16 or more workers per CTA): the seed and power
+    # passes of the generic pass modes against the exact spectrum of the X that
+    # the stored bases define
+    apc, dev = _apc(), _dev()
+    n, m = 2048, 32
+    A, _, b = inputs.gaussian_system(n, 35)
+    offs = inputs.even_offsets(n, m)
+    ctx = apc.apc_setup(torch.tensor(A, device=dev), torch.tensor(b, device=dev), offs, precision=prec,
+                        workers_per_warp=4)
+    Qs = [ctx.basis(i).cpu().numpy() for i in range(m)]
+    mu = np.linalg.eigvalsh(sum(Q @ Q.T for Q in Qs) / m)
+    e_lo, e_hi = ctx.spectral_bounds(steps=150, seed=11)
+    assert abs(e_hi - mu[-1]) <= 1e-5 * mu[-1]
+    assert e_lo >= mu[0] - 1e-6  # inside the spectrum (the square system's mu_min converges slowly)
