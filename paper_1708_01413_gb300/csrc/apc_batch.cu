@@ -76,6 +76,9 @@ namespace {
 using namespace apc;
 
 constexpr int kConsumerWarps = 8;
+// right-hand sides whose state a consumer thread loads together in the heavy-ball
+// and reverse-sweep row updates (their stores come after the loads)
+constexpr int kRowBatch = 4;
 constexpr int kProducerWarp = kConsumerWarps;       // issues the bulk copies
 constexpr int kMmaWarp = kConsumerWarps + 1;        // issues the tensor-core instructions
 constexpr int kThreads = 32 * (kConsumerWarps + 2);
@@ -658,16 +661,24 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
         char *xb = reinterpret_cast<char *>(d.Xb + grow), *mb = reinterpret_cast<char *>(d.Mb + grow);
         const uint32_t ns = opaque_u32(uint32_t(d.npad) * 8u);
 #pragma unroll
-        for (int q = 0; q < KP; ++q) {
-            float2 *lq = reinterpret_cast<float2 *>(mb + size_t(q) * ns);
-            float2 *bq = reinterpret_cast<float2 *>(xb + size_t(q) * ns);
-            const float2 l = __ldcg(lq), lb = __ldcg(bq);
-            const float2 mu = dfa(l, dfm(em, lb));
-            const float2 ln = dfm(om, mu);
-            const float2 lbn = dfa(dfa(dfm(e1, lb), dfm(gm, mu)), dfm(ng, make_float2(W[q], 0.0f)));
-            __stcg(lq, ln);
-            __stcg(bq, lbn);
-            xo[q] = dfa(ln, dfm(nx, lbn)).x;
+        for (int q0 = 0; q0 < KP; q0 += kRowBatch) {
+            // (ell, lbar) of kRowBatch right-hand sides loaded ahead of their stores
+            float2 l[kRowBatch], lb[kRowBatch];
+#pragma unroll
+            for (int j = 0; j < kRowBatch; ++j) {
+                l[j] = __ldcg(reinterpret_cast<const float2 *>(mb + size_t(q0 + j) * ns));
+                lb[j] = __ldcg(reinterpret_cast<const float2 *>(xb + size_t(q0 + j) * ns));
+            }
+#pragma unroll
+            for (int j = 0; j < kRowBatch; ++j) {
+                const int q = q0 + j;
+                const float2 mu = dfa(l[j], dfm(em, lb[j]));
+                const float2 ln = dfm(om, mu);
+                const float2 lbn = dfa(dfa(dfm(e1, lb[j]), dfm(gm, mu)), dfm(ng, make_float2(W[q], 0.0f)));
+                __stcg(reinterpret_cast<float2 *>(mb + size_t(q) * ns), ln);
+                __stcg(reinterpret_cast<float2 *>(xb + size_t(q) * ns), lbn);
+                xo[q] = dfa(ln, dfm(nx, lbn)).x;
+            }
         }
     } else if (hb) {
         // heavy ball on the preconditioned system (Sec. 4.3 update, Sec. 6):
@@ -677,14 +688,23 @@ __device__ void sweep_a_consumer(const Ring &R, Cursor &cur, uint32_t &mc, uint6
         char *xb = reinterpret_cast<char *>(d.Xb + grow), *mb = reinterpret_cast<char *>(d.Mb + grow);
         const uint32_t ns = opaque_u32(uint32_t(d.npad) * 8u);
 #pragma unroll
-        for (int q = 0; q < KP; ++q) {
-            float2 *mq = reinterpret_cast<float2 *>(mb + size_t(q) * ns);
-            float2 *xq = reinterpret_cast<float2 *>(xb + size_t(q) * ns);
-            const float2 zn = dfa(dfm(beta, __ldcg(mq)), make_float2(W[q], 0.0f));
-            const float2 xn = dfa(__ldcg(xq), dfm(nalpha, zn));
-            __stcg(mq, zn);
-            __stcg(xq, xn);
-            xo[q] = xn.x;
+        for (int q0 = 0; q0 < KP; q0 += kRowBatch) {
+            // (zeta, x) of kRowBatch right-hand sides loaded ahead of their stores
+            float2 z[kRowBatch], x[kRowBatch];
+#pragma unroll
+            for (int j = 0; j < kRowBatch; ++j) {
+                z[j] = __ldcg(reinterpret_cast<const float2 *>(mb + size_t(q0 + j) * ns));
+                x[j] = __ldcg(reinterpret_cast<const float2 *>(xb + size_t(q0 + j) * ns));
+            }
+#pragma unroll
+            for (int j = 0; j < kRowBatch; ++j) {
+                const int q = q0 + j;
+                const float2 zn = dfa(dfm(beta, z[j]), make_float2(W[q], 0.0f));
+                const float2 xn = dfa(x[j], dfm(nalpha, zn));
+                __stcg(reinterpret_cast<float2 *>(mb + size_t(q) * ns), zn);
+                __stcg(reinterpret_cast<float2 *>(xb + size_t(q) * ns), xn);
+                xo[q] = xn.x;
+            }
         }
     } else {
         // master: xbar' = (eta/m) S + (1 - eta) xbar   (initialisation: S / m)
@@ -778,18 +798,25 @@ __device__ void store_v(const SysDesc &d, int col, const float (&Y)[16 * MT], bo
     const uint32_t cs = opaque_u32(uint32_t(d.Cq) * 4u);
     const float gh = fin ? 1.0f : d.g_hi, gl = fin ? 0.0f : d.g_lo;
 #pragma unroll
-    for (int q = 0; q < KP; ++q) {
-        float *gq = reinterpret_cast<float *>(gc + size_t(q) * cs);
-        const float y = Y[q];
-        __stcg(gq, __ldcg(gq) + fmaf(gh, y, gl * y));
-        if (!fin) {
-            const float y1 = __shfl_down_sync(0xffffffffu, y, 1);
-            if ((lane & 1) == 0) {
-                uint32_t w[kPlanesA];
-                split2<kPlanesA>(y, y1, w);
+    for (int q0 = 0; q0 < KP; q0 += kRowBatch) {
+        // dL/dc of kRowBatch right-hand sides loaded ahead of their stores
+        float g[kRowBatch];
 #pragma unroll
-                for (int p = 0; p < kPlanesA; ++p)
-                    __stcg(reinterpret_cast<uint32_t *>(d.Zop + op_offset(NA, p * KP + q, col)), w[p]);
+        for (int j = 0; j < kRowBatch; ++j) g[j] = __ldcg(reinterpret_cast<const float *>(gc + size_t(q0 + j) * cs));
+#pragma unroll
+        for (int j = 0; j < kRowBatch; ++j) {
+            const int q = q0 + j;
+            const float y = Y[q];
+            __stcg(reinterpret_cast<float *>(gc + size_t(q) * cs), g[j] + fmaf(gh, y, gl * y));
+            if (!fin) {
+                const float y1 = __shfl_down_sync(0xffffffffu, y, 1);
+                if ((lane & 1) == 0) {
+                    uint32_t w[kPlanesA];
+                    split2<kPlanesA>(y, y1, w);
+#pragma unroll
+                    for (int p = 0; p < kPlanesA; ++p)
+                        __stcg(reinterpret_cast<uint32_t *>(d.Zop + op_offset(NA, p * KP + q, col)), w[p]);
+                }
             }
         }
     }
