@@ -424,11 +424,15 @@ __device__ __forceinline__ bool combine_parts(float (&v)[KP], float *part, size_
     old = __shfl_sync(0xffffffffu, old, 0);
     if (old != np - 1) return false;
     __threadfence();
+    // part after part, each part's KP values loaded together (one round trip
+    // per part instead of one per value); every sum still adds the parts in
+    // part order, starting from zero
 #pragma unroll
-    for (int q = 0; q < KP; ++q) {
-        float t = 0.0f;
-        for (int pp = 0; pp < np; ++pp) t += __ldcg(part + (size_t(pp) * KP + q) * stride);
-        v[q] = t;
+    for (int q = 0; q < KP; ++q) v[q] = 0.0f;
+    for (int pp = 0; pp < np; ++pp) {
+        const float *pq = part + size_t(pp) * KP * stride;
+#pragma unroll
+        for (int q = 0; q < KP; ++q) v[q] += __ldcg(pq + size_t(q) * stride);
     }
     __syncwarp();
     if (lane == 0) atomicExch(cnt, 0);
